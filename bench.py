@@ -1,0 +1,319 @@
+"""Benchmark: simulated cycles per second of the BSP RTL simulator on GB300.
+
+Headline workload: the mid netlist (200k ops, 20k registers: 30% 1-bit,
+40% 32-bit, 30% 64-bit, depth 60, two 512x64-bit synchronous RAMs), one
+instance, 100,000 simulated cycles, persistent kernel with a grid barrier.
+A step is one sim_step of `--cycles` simulated cycles (default 10,000), so
+the default 10 timed steps simulate the full 100k-cycle workload.
+
+Also reported in the same JSON line (`rows`): the launch-per-cycle baseline
+and its CUDA-graph replay on the same workload, and the batched workload
+(the same netlist x 4,096 independently seeded instances, lane = instance).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--cycles C] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "simulated cycles/s (1 instance) and instance-cycles/s (batched), p50/p99 job latency"
+UNIT = "simulated cycles/s"
+WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
+            "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
+            "100k cycles; persistent kernel, grid barrier")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+# Integer issue peak (no measured integer peak exists): 152 SMs x 4 SM
+# sub-partitions x 32 lanes x 1 instruction/clock at the maximum SM clock.
+def alu_peak_ops(p):
+    return 152 * 4 * 32 * float(p.get("sm_max_mhz", 2070.0)) * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    if n_gpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, 0, None
+    import torch
+    import torch.distributed as dist
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return dist.get_rank(), dist.get_world_size(), local, dist
+
+
+def barrier(dist):
+    import torch
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+
+
+def max_over_ranks(dist, x):
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_steps(batch, stream, steps, warmup, cycles, flush):
+    """Device-timed steps (CUDA events on the batch's stream), L2 flushed between steps."""
+    import torch
+    for _ in range(warmup):
+        batch.step(cycles)
+    batch.sync()
+    ms = []
+    k0 = batch.launch_info()["kernels_launched"]
+    for _ in range(steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch.step(cycles)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    batch.sync()
+    launches = batch.launch_info()["kernels_launched"] - k0
+    return ms, launches
+
+
+def run_cpu_baseline(path, cycles, seed=42):
+    import oracle
+    net = oracle.Net(path)
+    s = oracle.Sim(net, seed, 0)
+    t = time.perf_counter()
+    s.run(cycles)
+    dt = time.perf_counter() - t
+    return cycles / dt, dt
+
+
+def reference_arm(args, rank):
+    """The oracle, as it stands, on the host cores (the reference arm)."""
+    if rank != 0:
+        return
+    from paper_2403_04714_gb300 import netgen
+    import oracle
+    oracle.build()
+    path = netgen.cached_netlist("mid")
+    per_step = args.ref_cycles
+    net = oracle.Net(path)
+    s = oracle.Sim(net, 42, 0)
+    s.run(per_step * args.warmup)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        s.run(per_step)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = args.steps * per_step / total
+    sample = f"{per_step} cycles of the mid netlist (1 instance) per step on one host core"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--cycles", type=int, default=10_000, help="simulated cycles per step")
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--ref-cycles", type=int, default=300)
+    ap.add_argument("--cpu-cycles", type=int, default=3000, help="oracle sample for cpu_baseline")
+    ap.add_argument("--batched-cycles", type=int, default=100)
+    ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
+    args = ap.parse_args()
+    rank, world, local, dist = (0, 1, 0, None)
+    if args.impl == "reference":
+        if "RANK" in os.environ and int(os.environ["RANK"]) != 0:
+            return
+        reference_arm(args, 0)
+        return
+    rank, world, local, dist = dist_setup(args.gpus)
+
+    import numpy as np
+    import torch
+    from paper_2403_04714_gb300 import netgen, sim
+    from paper_2403_04714_gb300.build import build
+    if rank == 0:
+        build()
+    barrier(dist)
+    path = netgen.cached_netlist("mid")
+    text = open(path, "rb").read()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    p = peaks()
+
+    # ---- headline: single instance, persistent kernel --------------------------
+    nl = sim.Netlist(text, mode="lane_op")
+    info = nl.info()
+    b = sim.Batch(nl, 1, seed=42 + rank, stream=stream)
+    barrier(dist)
+    with ClockSampler(local) as clk:
+        ms, launches = time_steps(b, stream, args.steps, args.warmup, args.cycles, flush)
+    total_s = max_over_ranks(dist, sum(ms) / 1000.0)
+    value = world * args.steps * args.cycles / total_s
+    per_launch_s = sum(ms) / 1000.0 / max(1, launches)
+    cycles_per_launch = args.steps * args.cycles / max(1, launches)
+    ops = info["n_ops"]
+    achieved = ops * cycles_per_launch / per_launch_s
+    peak = alu_peak_ops(p)
+    geo = b.launch_info()
+
+    # ---- e2e through host buffers: held inputs in, per-instance digest out ------
+    b2 = sim.Batch(nl, 1, seed=42 + rank, stream=stream)
+    n_in = info["n_inputs"]
+    held = np.arange(n_in, dtype=np.uint64).reshape(1, n_in) * np.uint64(0x9E3779B1)
+    held_pinned = torch.from_numpy(held).pin_memory().numpy()
+    out_pinned = torch.zeros(1, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
+    for _ in range(args.warmup):
+        b2.step_host(args.cycles, held_pinned, out_pinned)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b2.step_host(args.cycles, held_pinned, out_pinned)
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
+    e2e = {"value": world * args.steps * args.cycles / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(held.nbytes), "d2h_bytes_per_step": 8,
+           "call": "sim_step_host (all inputs held from pinned host memory, state digest read back)"}
+    del b2
+
+    rows = {}
+    if not args.no_rows:
+        # launch-per-cycle baseline and its graph replay, same workload
+        for kname in ("per_cycle", "graph"):
+            nlk = sim.Netlist(text, mode="lane_op", kernel=kname)
+            bk = sim.Batch(nlk, 1, seed=42, stream=stream)
+            cyc = min(args.cycles, 2000)
+            msk, lk = time_steps(bk, stream, 3, 1, cyc, flush)
+            rows[f"single_{kname}"] = {"value": 3 * cyc / (sum(msk) / 1000.0), "unit": UNIT,
+                                       "cycles_timed": 3 * cyc, "kernels": lk}
+            del bk, nlk
+        # batched: same netlist x 4096 instances, lane = instance
+        nlb = sim.Netlist(text, mode="lane_inst")
+        bb = sim.Batch(nlb, 4096, seed=42, stream=stream)
+        msb, lb = time_steps(bb, stream, 3, 1, args.batched_cycles, flush)
+        sec = sum(msb) / 1000.0
+        ib = nlb.info()
+        rows["batched_4096"] = {
+            "value": 3 * args.batched_cycles * 4096 / sec, "unit": "instance-cycles/s",
+            "cycles_timed": 3 * args.batched_cycles, "kernels": lb, "launch": bb.launch_info(),
+            "processes": ib["n_processes"], "ops_per_cycle": ib["n_ops"],
+            "alu_frac": ib["n_ops"] * 3 * args.batched_cycles * 4096 / sec / peak,
+        }
+        del bb, nlb
+
+    # ---- CPU baseline: the oracle on one host core, bounded sample -------------
+    cpu = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        v, dt = run_cpu_baseline(path, args.cpu_cycles)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {args.cpu_cycles} cycles of the mid netlist, 1 instance ({dt:.1f} s)"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "cycles_per_step": args.cycles, "instances": 1,
+                       "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
+                       "processes": info["n_processes"], "launch": geo},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "k_cycles<LANE_OP> (persistent)",
+                         "note": "word ops (algorithmic, unduplicated) per second; peak = 152 SMs x 128 lanes "
+                                 "x max SM clock; single-instance BSP is latency-bound"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+            "rows": rows,
+            "netlist": {k: info[k] for k in ("n_ops", "n_regs", "n_fibers", "n_processes", "fiber_cost_sum",
+                                             "process_cost_sum", "process_cost_max", "fiber_cost_max",
+                                             "max_bundles", "cut_words")},
+        }
+        print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * sim.h -- C ABI of the GB300 BSP RTL simulator.
+ *
+ * The simulator runs the per-clock-cycle bulk-synchronous evaluation of a
+ * partitioned word-level netlist (Parendi, Sec. 3.2 "BSP RTL Simulation" and
+ * Sec. 5.1 "Partitioning"): every register's combinational cone is a fiber,
+ * fibers are merged into processes by submodular load balancing, each
+ * process computes its registers' next values from the current values, the
+ * next values are committed to double-buffered state, and one grid-wide
+ * barrier separates simulated cycles.
+ *
+ * Conventions for every function below:
+ *   - the return value is SIM_OK (0) or a negative SIM_ERR_* code, and
+ *     sim_last_error() then holds a message for the calling thread;
+ *   - handles are created and owned by the library; the caller releases
+ *     them with the matching *_destroy, batches before their netlist;
+ *   - buffers passed in are copied before the call returns, buffers passed
+ *     out are caller-owned host memory of the stated size;
+ *   - no C++ exception ever crosses this boundary.
+ *
+ * Netlist text format (`rtlnet 1`): see the module docstring of
+ * paper_2403_04714_gb300/netgen.py.  Inputs, registers, memories and nodes are
+ * numbered from 0 in file order.  Semantics per simulated cycle: inputs are
+ * drawn (or held), all nodes are evaluated from current register and memory
+ * values, registers take their next-state values, then memory write ports
+ * apply in ascending port order (the highest port wins an address).
+ */
+#ifndef GB300_RTLSIM_SIM_H
+#define GB300_RTLSIM_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+enum {
+    SIM_OK = 0,
+    SIM_ERR_PARSE = -1,      /* malformed netlist text */
+    SIM_ERR_COMB_LOOP = -2,  /* combinational cycle (paper Sec. 5.3: compile fails) */
+    SIM_ERR_WIDTH = -3,      /* width/slice/concat/compare inconsistency */
+    SIM_ERR_CAPACITY = -4,   /* a process does not fit the per-warp on-chip budget (Sec. 5.1 stage 4) */
+    SIM_ERR_OOM = -5,        /* device or host allocation failed */
+    SIM_ERR_TIMEOUT = -6,    /* a grid barrier wait ran past its limit */
+    SIM_ERR_CUDA = -7,       /* a CUDA runtime call failed */
+    SIM_ERR_BADARG = -8,     /* argument out of range or null */
+    SIM_ERR_ADMISSION = -9,  /* job larger than the server's memory cap */
+    SIM_ERR_STATE = -10      /* call not valid in the current state */
+};
+
+/* signal kinds for sim_poke / sim_peek */
+enum { SIM_SIG_INPUT = 0, SIM_SIG_REG = 1 };
+
+/* How a warp maps onto the netlist.
+ *   LANE_OP:   one warp runs one process of one instance; its 32 lanes run
+ *              independent nodes of the same schedule step (single instance).
+ *   LANE_INST: one warp runs one process for 32 instances, lane = instance,
+ *              with instance-minor state (batched stimulus instances).
+ *   AUTO:      LANE_INST when n_inst >= 32, else LANE_OP. */
+enum { SIM_MODE_AUTO = 0, SIM_MODE_LANE_OP = 1, SIM_MODE_LANE_INST = 2 };
+
+/* How cycles are launched.
+ *   PERSISTENT:  one cooperative launch per sim_step keeps every process
+ *                resident and crosses cycles with a flag-based grid barrier.
+ *   PER_CYCLE:   one kernel launch per simulated cycle; the launch boundary
+ *                is the barrier (the plain baseline).
+ *   PER_CYCLE_GRAPH: the PER_CYCLE launch chain captured once into a CUDA
+ *                graph and replayed. */
+enum { SIM_KERNEL_PERSISTENT = 0, SIM_KERNEL_PER_CYCLE = 1, SIM_KERNEL_PER_CYCLE_GRAPH = 2 };
+
+typedef struct sim_config {
+    uint32_t struct_size;       /* sizeof(sim_config) */
+    int32_t mode;               /* SIM_MODE_* */
+    int32_t kernel;             /* SIM_KERNEL_* */
+    uint32_t target_processes;  /* SLB target count; 0 = one per resident warp */
+    uint32_t warps_per_cta;     /* 0 = autotuned */
+    uint32_t max_slots;         /* per-process value-slot cap; 0 = from the shared-memory budget */
+    uint32_t digest_capacity;   /* per-cycle digest ring length in cycles; 0 = digests off */
+    uint32_t timeout_ms;        /* grid-barrier wait limit (default 2000) */
+    uint64_t big_array_bytes;   /* SLB stage-1 threshold (paper default 128 KiB) */
+    uint32_t disable_stage3;    /* testing: skip the conservative merge */
+    uint32_t seed_partition;    /* testing: 0 = SLB; else a random partition with this seed */
+    uint32_t reserved[8];
+} sim_config;
+
+typedef struct sim_netlist_info {
+    uint32_t n_inputs, n_regs, n_mems, n_wports;
+    uint64_t n_nodes;           /* all nodes including leaves */
+    uint64_t n_ops;             /* combinational operators */
+    uint32_t n_fibers;          /* sinks: registers plus memories with write ports */
+    uint32_t n_processes;       /* after SLB */
+    uint64_t fiber_cost_sum;    /* sum of fiber costs (duplication at one fiber per process) */
+    uint64_t process_cost_sum;  /* sum of process costs after merging (duplicated work) */
+    uint64_t process_cost_max;  /* straggler process cost (paper Sec. 4.3, t_comp bound) */
+    uint64_t fiber_cost_max;    /* slowest fiber: the lower bound max_i t_i */
+    uint32_t max_bundles;       /* longest LANE_OP schedule in 32-wide steps */
+    uint32_t max_slots;         /* largest value-slot count of a process */
+    uint64_t instr_count;       /* lowered instructions over all processes */
+    uint64_t cut_words;         /* register words read across processes per cycle */
+} sim_netlist_info;
+
+typedef struct sim_netlist sim_netlist;
+typedef struct sim_batch sim_batch;
+
+/* Fill cfg with defaults (AUTO mode, persistent kernel, digests off). */
+void sim_config_default(sim_config *cfg);
+
+/* Parse, check, partition (fibers -> SLB processes, paper Sec. 5.1) and lower
+ * a netlist.  `text` holds `len` bytes of rtlnet text (copied).  `cfg` may be
+ * NULL for defaults.  Errors: PARSE, COMB_LOOP, WIDTH, CAPACITY, BADARG, OOM. */
+int sim_load_netlist(const void *text, size_t len, const sim_config *cfg, sim_netlist **out);
+int sim_netlist_get_info(const sim_netlist *nl, sim_netlist_info *out);
+void sim_netlist_destroy(sim_netlist *nl);
+
+/* Introspection of the compiled program (tests and tools).  With out == NULL
+ * *bytes receives the table size; otherwise min(*bytes, size) bytes are
+ * copied to out and *bytes receives the size.  Tables (`which`):
+ *   0 LANE_OP bundles (16-byte instructions, 32 per bundle)
+ *   1 LANE_OP first bundle of each process (u32)   2 LANE_OP bundle counts (u32)
+ *   3 LANE_INST instructions (16 bytes)            4 LANE_INST first instruction (u32)
+ *   5 LANE_INST instruction counts (u32)           6 process of each fiber (i32)
+ *   7 sink of each fiber: register r >= 0, or -1-m for memory m (i32)
+ *   8 cost of each fiber (u64)                     9 cost of each process (u64)
+ *  10 register storage class (u8: 0 1-bit, 1 <=32-bit, 2 <=64-bit)
+ *  11 register index within its class (u32)
+ *  12 LANE_OP slot count of each process (u32)    13 LANE_INST slot count (u32)
+ * Errors: BADARG. */
+int sim_netlist_table(const sim_netlist *nl, int32_t which, void *out, size_t *bytes);
+
+/* Allocate device state for n_inst instances (cudaMalloc), initialised to the
+ * netlist's register init values and memory images, cycle 0.  Instance i's
+ * stimulus key is output i+1 of the SplitMix64 stream seeded with `seed`.
+ * `cuda_stream` is a cudaStream_t (NULL = legacy default stream); every
+ * device operation of the batch is ordered on it.  Errors: BADARG, OOM, CUDA. */
+int sim_create_instances(sim_netlist *nl, uint32_t n_inst, uint64_t seed, void *cuda_stream,
+                         sim_batch **out);
+void sim_batch_destroy(sim_batch *b);
+
+/* Input: hold `value` (overrides the stimulus from the next cycle on, until
+ * sim_unpoke).  Register: overwrite its current value.  Takes effect before
+ * the next sim_step.  Value is reduced to the signal width. */
+int sim_poke(sim_batch *b, uint32_t inst, int32_t kind, uint32_t index, uint64_t value);
+int sim_unpoke(sim_batch *b, uint32_t inst, uint32_t input);
+int sim_poke_mem(sim_batch *b, uint32_t inst, uint32_t mem, uint64_t addr, uint64_t value);
+
+/* Enqueue n_cycles simulated cycles on the batch's stream (asynchronous).
+ * A barrier time-out is reported by the next sim_sync. */
+int sim_step(sim_batch *b, uint64_t n_cycles);
+int sim_sync(sim_batch *b);
+
+/* Read state after the last completed cycle (synchronises the stream). */
+int sim_peek(sim_batch *b, uint32_t inst, int32_t kind, uint32_t index, uint64_t *out);
+int sim_peek_mem(sim_batch *b, uint32_t inst, uint32_t mem, uint64_t addr, uint64_t *out);
+int sim_peek_regs(sim_batch *b, uint32_t inst, uint64_t *out /* n_regs values */);
+int sim_cycle(sim_batch *b, uint64_t *out);
+
+/* Digest of the current state of each instance, computed on the device:
+ * sum over registers r of mix(H(r) ^ reg[r]) plus sum over memory words of
+ * mix(H(2^40 + m*2^24 + a) ^ mem[m][a]) modulo 2^64, H(x) = x*gamma + 1,
+ * mix = SplitMix64 output function.  out holds n_inst values. */
+int sim_state_digests(sim_batch *b, uint64_t *out);
+
+/* Per-cycle digests (ring of sim_config.digest_capacity cycles) are kept for
+ * the instances listed here (default: instance 0).  Call before sim_step. */
+int sim_track_digests(sim_batch *b, const uint32_t *insts, uint32_t n);
+/* Digests of states first..first+n-1 of a tracked instance (state t = after
+ * t cycles), still inside the ring.  Synchronises. */
+int sim_digests(sim_batch *b, uint32_t inst, uint64_t first_cycle, uint64_t n, uint64_t *out);
+
+/* One end-to-end step through host memory: copies n_inst*n_inputs held input
+ * values (NULL = free-running stimulus) host->device, runs n_cycles, and
+ * copies the n_inst final state digests device->host.  Synchronises. */
+int sim_step_host(sim_batch *b, uint64_t n_cycles, const uint64_t *held_inputs, uint64_t *out_digests);
+
+/* Checkpoint: registers, memories, held inputs and the cycle counter.  The
+ * blob is malloc'd by the library; release it with sim_free_blob. */
+int sim_save(sim_batch *b, void **blob, size_t *len);
+int sim_restore(sim_batch *b, const void *blob, size_t len);
+void sim_free_blob(void *blob);
+
+/* Launch geometry actually used by the last sim_step: ctas, warps/cta,
+ * processes, tasks per cycle; and how many kernels it launched. */
+int sim_launch_info(sim_batch *b, uint32_t *ctas, uint32_t *warps_per_cta, uint32_t *tasks_per_cycle,
+                    uint64_t *kernels_launched);
+
+/* Testing hook: make one CTA skip its barrier arrival once on the next
+ * persistent sim_step, so the other CTAs' bounded waits expire and the step
+ * returns SIM_ERR_TIMEOUT.  No fault, trap or unbounded wait is involved. */
+int sim_debug_skip_arrival(sim_batch *b, uint32_t timeout_ms);
+
+const char *sim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

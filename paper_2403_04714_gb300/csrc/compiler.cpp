@@ -1,0 +1,1004 @@
+// compiler.cpp -- parse/check, fibers, SLB partitioning and lowering.
+#include "compiler.hpp"
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <queue>
+#include <random>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "../../include/sim.h"
+
+namespace rtl {
+
+// ------------------------------------------------------------------------
+// Parser
+// ------------------------------------------------------------------------
+namespace {
+
+struct Cursor {
+    const char* p;
+    const char* end;
+    long line = 1;
+};
+
+static const char* kOpNames[OP_COUNT] = {
+    "input", "reg", "const", "memrd", "add", "sub", "mul", "and", "or", "xor",
+    "shl", "shr", "eq", "lt", "mux", "slice", "concat"};
+
+inline bool is_space(char c) { return c == ' ' || c == '\t' || c == '\r'; }
+
+// Split one line into tokens (pointer, length); stops at '#'.
+int split_line(Cursor& cur, const char** tok, int* tlen, int maxtok) {
+    int nt = 0;
+    while (cur.p < cur.end && *cur.p != '\n') {
+        while (cur.p < cur.end && is_space(*cur.p)) cur.p++;
+        if (cur.p >= cur.end || *cur.p == '\n') break;
+        if (*cur.p == '#') {
+            while (cur.p < cur.end && *cur.p != '\n') cur.p++;
+            break;
+        }
+        const char* s = cur.p;
+        while (cur.p < cur.end && !is_space(*cur.p) && *cur.p != '\n') cur.p++;
+        if (nt < maxtok) {
+            tok[nt] = s;
+            tlen[nt] = int(cur.p - s);
+        }
+        nt++;
+    }
+    if (cur.p < cur.end && *cur.p == '\n') cur.p++;
+    return nt;
+}
+
+bool tok_u64(const char* s, int n, uint64_t& out) {
+    if (n <= 0 || n > 40) return false;
+    char buf[48];
+    memcpy(buf, s, n);
+    buf[n] = 0;
+    if (buf[0] == '-') return false;
+    char* e = nullptr;
+    out = strtoull(buf, &e, 0);
+    return *e == 0;
+}
+
+bool tok_i32(const char* s, int n, int32_t& out) {
+    uint64_t v;
+    if (!tok_u64(s, n, v) || v > 0x7fffffffULL) return false;
+    out = int32_t(v);
+    return true;
+}
+
+bool tok_eq(const char* s, int n, const char* lit) { return int(strlen(lit)) == n && !memcmp(s, lit, n); }
+
+inline uint64_t mask_w(int w) { return w >= 64 ? ~0ULL : ((1ULL << w) - 1); }
+
+}  // namespace
+
+int parse_netlist(const char* text, size_t len, Netlist& nl, std::string& err) {
+    Cursor cur{text, text + len};
+    const char* tok[8];
+    int tl[8];
+    bool header = false, ended = false;
+    std::vector<std::pair<int32_t, int32_t>> nexts;
+    char msg[256];
+    auto fail = [&](int code, const char* what) {
+        snprintf(msg, sizeof msg, "line %ld: %s", cur.line, what);
+        err = msg;
+        return code;
+    };
+    while (cur.p < cur.end) {
+        int nt = split_line(cur, tok, tl, 8);
+        long line = cur.line++;
+        (void)line;
+        if (nt == 0) continue;
+        if (ended) return fail(SIM_ERR_PARSE, "content after end");
+        if (nt > 8) return fail(SIM_ERR_PARSE, "too many fields");
+        if (!header) {
+            if (nt != 2 || !tok_eq(tok[0], tl[0], "rtlnet") || !tok_eq(tok[1], tl[1], "1"))
+                return fail(SIM_ERR_PARSE, "expected 'rtlnet 1'");
+            header = true;
+            continue;
+        }
+        const char* k = tok[0];
+        int kl = tl[0];
+        if (tok_eq(k, kl, "n")) {
+            Node nd;
+            int32_t w;
+            if (nt < 3 || !tok_i32(tok[2], tl[2], w)) return fail(SIM_ERR_PARSE, "bad node");
+            int op = -1;
+            for (int i = 0; i < OP_COUNT; i++)
+                if (tok_eq(tok[1], tl[1], kOpNames[i])) op = i;
+            if (op < 0) return fail(SIM_ERR_PARSE, "unknown op");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "node width out of range");
+            nd.op = uint8_t(op);
+            nd.w = uint8_t(w);
+            int want = op == OP_MUX ? 3 : (op == OP_INPUT || op == OP_REG || op == OP_CONST) ? 1 : 2;
+            if (nt != 3 + want) return fail(SIM_ERR_PARSE, "wrong operand count");
+            if (op == OP_CONST) {
+                if (!tok_u64(tok[3], tl[3], nd.k)) return fail(SIM_ERR_PARSE, "bad constant");
+                nd.k &= mask_w(w);
+            } else {
+                int32_t v[3] = {-1, -1, -1};
+                for (int i = 0; i < want; i++)
+                    if (!tok_i32(tok[3 + i], tl[3 + i], v[i])) return fail(SIM_ERR_PARSE, "bad operand");
+                nd.a = v[0];
+                nd.b = v[1];
+                nd.c = v[2];
+            }
+            nl.nodes.push_back(nd);
+        } else if (tok_eq(k, kl, "in")) {
+            int32_t w;
+            if (nt < 2 || !tok_i32(tok[1], tl[1], w)) return fail(SIM_ERR_PARSE, "bad in");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "input width out of range");
+            nl.in_w.push_back(uint8_t(w));
+        } else if (tok_eq(k, kl, "reg")) {
+            int32_t w;
+            uint64_t init;
+            if (nt < 3 || !tok_i32(tok[1], tl[1], w) || !tok_u64(tok[2], tl[2], init))
+                return fail(SIM_ERR_PARSE, "bad reg");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "register width out of range");
+            nl.reg_w.push_back(uint8_t(w));
+            nl.reg_init.push_back(init & mask_w(w));
+            nl.reg_next.push_back(-1);
+        } else if (tok_eq(k, kl, "mem")) {
+            int32_t lg, w;
+            if (nt < 3 || !tok_i32(tok[1], tl[1], lg) || !tok_i32(tok[2], tl[2], w))
+                return fail(SIM_ERR_PARSE, "bad mem");
+            if (lg > 24) return fail(SIM_ERR_WIDTH, "memory depth out of range");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "memory width out of range");
+            nl.mem_lg.push_back(uint8_t(lg));
+            nl.mem_w.push_back(uint8_t(w));
+            nl.mem_init.emplace_back();
+        } else if (tok_eq(k, kl, "next")) {
+            int32_t r, x;
+            if (nt != 3 || !tok_i32(tok[1], tl[1], r) || !tok_i32(tok[2], tl[2], x))
+                return fail(SIM_ERR_PARSE, "bad next");
+            nexts.emplace_back(r, x);
+        } else if (tok_eq(k, kl, "wport")) {
+            int32_t v[4];
+            if (nt != 5) return fail(SIM_ERR_PARSE, "bad wport");
+            for (int i = 0; i < 4; i++)
+                if (!tok_i32(tok[1 + i], tl[1 + i], v[i])) return fail(SIM_ERR_PARSE, "bad wport");
+            nl.wports.push_back({v[0], v[1], v[2], v[3]});
+        } else if (tok_eq(k, kl, "minit")) {
+            int32_t m;
+            uint64_t a, v;
+            if (nt != 4 || !tok_i32(tok[1], tl[1], m) || !tok_u64(tok[2], tl[2], a) || !tok_u64(tok[3], tl[3], v))
+                return fail(SIM_ERR_PARSE, "bad minit");
+            if (m >= int32_t(nl.mem_lg.size()) || a >= (1ULL << nl.mem_lg[m]))
+                return fail(SIM_ERR_PARSE, "minit out of range");
+            nl.mem_init[m].push_back({uint32_t(a), v & mask_w(nl.mem_w[m])});
+        } else if (tok_eq(k, kl, "end")) {
+            ended = true;
+        } else {
+            return fail(SIM_ERR_PARSE, "unknown item");
+        }
+    }
+    if (!header) { err = "missing 'rtlnet 1' header"; return SIM_ERR_PARSE; }
+    if (!ended) { err = "missing 'end'"; return SIM_ERR_PARSE; }
+
+    // ---- structural checks ------------------------------------------------
+    const int32_t N = int32_t(nl.nodes.size());
+    for (auto& [r, x] : nexts) {
+        if (r < 0 || r >= int32_t(nl.reg_w.size())) { err = "next of unknown register"; return SIM_ERR_PARSE; }
+        if (nl.reg_next[r] >= 0) { err = "register has two next nodes"; return SIM_ERR_PARSE; }
+        if (x < 0 || x >= N) { err = "next node out of range"; return SIM_ERR_PARSE; }
+        nl.reg_next[r] = x;
+    }
+    for (size_t r = 0; r < nl.reg_next.size(); r++)
+        if (nl.reg_next[r] < 0) { err = "register " + std::to_string(r) + " has no next node"; return SIM_ERR_PARSE; }
+    for (auto& wp : nl.wports)
+        if (wp.mem < 0 || wp.mem >= int32_t(nl.mem_lg.size()) || wp.en >= N || wp.addr >= N || wp.data >= N) {
+            err = "write port out of range";
+            return SIM_ERR_PARSE;
+        }
+    nl.mem_ports.assign(nl.mem_lg.size(), {});
+    for (size_t p = 0; p < nl.wports.size(); p++) nl.mem_ports[nl.wports[p].mem].push_back(int32_t(p));
+
+    std::vector<int32_t> indeg(N, 0);
+    nl.n_ops = 0;
+    for (int32_t i = 0; i < N; i++) {
+        Node& d = nl.nodes[i];
+        auto bad = [&](const char* what) { err = "node " + std::to_string(i) + ": " + what; };
+        switch (d.op) {
+        case OP_INPUT:
+            if (d.a >= int32_t(nl.in_w.size())) { bad("input out of range"); return SIM_ERR_PARSE; }
+            if (d.w != nl.in_w[d.a]) { bad("input width mismatch"); return SIM_ERR_WIDTH; }
+            continue;
+        case OP_REG:
+            if (d.a >= int32_t(nl.reg_w.size())) { bad("register out of range"); return SIM_ERR_PARSE; }
+            if (d.w != nl.reg_w[d.a]) { bad("register width mismatch"); return SIM_ERR_WIDTH; }
+            continue;
+        case OP_CONST:
+            continue;
+        case OP_MEMRD:
+            if (d.a >= int32_t(nl.mem_lg.size()) || d.b >= N) { bad("memrd out of range"); return SIM_ERR_PARSE; }
+            if (d.w != nl.mem_w[d.a]) { bad("memrd width mismatch"); return SIM_ERR_WIDTH; }
+            indeg[i] = 1;
+            break;
+        case OP_SLICE:
+            if (d.a >= N) { bad("operand out of range"); return SIM_ERR_PARSE; }
+            if (d.b + int(d.w) > int(nl.nodes[d.a].w)) { bad("slice out of range"); return SIM_ERR_WIDTH; }
+            indeg[i] = 1;
+            break;
+        case OP_CONCAT:
+            if (d.a >= N || d.b >= N) { bad("operand out of range"); return SIM_ERR_PARSE; }
+            if (int(d.w) != int(nl.nodes[d.a].w) + int(nl.nodes[d.b].w)) { bad("concat width mismatch"); return SIM_ERR_WIDTH; }
+            indeg[i] = 2;
+            break;
+        case OP_EQ:
+        case OP_LT:
+            if (d.w != 1) { bad("compare must be 1 bit"); return SIM_ERR_WIDTH; }
+            [[fallthrough]];
+        default:
+            if (d.a >= N || d.b >= N || (d.op == OP_MUX && d.c >= N)) { bad("operand out of range"); return SIM_ERR_PARSE; }
+            indeg[i] = d.op == OP_MUX ? 3 : 2;
+        }
+        nl.n_ops++;
+    }
+    // consumers (CSR) and Kahn order; level = longest path from a leaf
+    auto for_operands = [&](const Node& d, auto&& f) {
+        switch (d.op) {
+        case OP_INPUT: case OP_REG: case OP_CONST: return;
+        case OP_MEMRD: f(d.b); return;
+        case OP_SLICE: f(d.a); return;
+        case OP_MUX: f(d.a); f(d.b); f(d.c); return;
+        default: f(d.a); f(d.b); return;
+        }
+    };
+    std::vector<int64_t> off(N + 1, 0);
+    for (int32_t i = 0; i < N; i++) for_operands(nl.nodes[i], [&](int32_t o) { off[o + 1]++; });
+    for (int32_t i = 0; i < N; i++) off[i + 1] += off[i];
+    std::vector<int32_t> users(off[N]);
+    {
+        std::vector<int64_t> fill(off.begin(), off.end() - 1);
+        for (int32_t i = 0; i < N; i++) for_operands(nl.nodes[i], [&](int32_t o) { users[fill[o]++] = i; });
+    }
+    nl.level.assign(N, 0);
+    std::vector<int32_t> q;
+    q.reserve(N);
+    for (int32_t i = 0; i < N; i++)
+        if (indeg[i] == 0) q.push_back(i);
+    for (size_t h = 0; h < q.size(); h++) {
+        int32_t i = q[h];
+        for (int64_t u = off[i]; u < off[i + 1]; u++) {
+            int32_t j = users[u];
+            nl.level[j] = std::max(nl.level[j], nl.level[i] + 1);
+            if (--indeg[j] == 0) q.push_back(j);
+        }
+    }
+    if (int32_t(q.size()) != N) { err = "combinational loop"; return SIM_ERR_COMB_LOOP; }
+    return SIM_OK;
+}
+
+// ------------------------------------------------------------------------
+// Fibers and costs
+// ------------------------------------------------------------------------
+// Estimated issue cost of one node in the device interpreter (the paper
+// leaves its cost estimate unstated, Sec. 5.1): one unit per simple op,
+// more for 64-bit multiply, the stimulus hash and memory reads.
+uint64_t node_cost(const Netlist& nl, int32_t id) {
+    const Node& d = nl.nodes[id];
+    switch (d.op) {
+    case OP_CONST: return 1;
+    case OP_INPUT: return 3;
+    case OP_MEMRD: return 3;
+    case OP_MUL: return d.w > 32 ? 3 : 2;
+    default: return 1;
+    }
+}
+
+static uint64_t sink_cost(const Netlist& nl, const Fiber& f) {
+    if (f.reg >= 0) return 1;                                 // the register store
+    return uint64_t(nl.mem_ports[f.mem].size()) * 2 + 2;       // write records + commit
+}
+
+void extract_fibers(const Netlist& nl, std::vector<Fiber>& out) {
+    const int32_t N = int32_t(nl.nodes.size());
+    std::vector<uint32_t> stamp(N, 0);
+    uint32_t epoch = 0;
+    std::vector<int32_t> stack;
+    auto crawl = [&](Fiber& f, int32_t root) {
+        stack.push_back(root);
+        while (!stack.empty()) {
+            int32_t i = stack.back();
+            stack.pop_back();
+            if (stamp[i] == epoch) continue;
+            stamp[i] = epoch;
+            f.nodes.push_back(i);
+            const Node& d = nl.nodes[i];
+            switch (d.op) {
+            case OP_INPUT: case OP_REG: case OP_CONST: break;
+            case OP_MEMRD: stack.push_back(d.b); break;
+            case OP_SLICE: stack.push_back(d.a); break;
+            case OP_MUX: stack.push_back(d.a); stack.push_back(d.b); stack.push_back(d.c); break;
+            default: stack.push_back(d.a); stack.push_back(d.b);
+            }
+        }
+    };
+    out.clear();
+    out.reserve(nl.reg_w.size() + nl.mem_lg.size());
+    // one fiber per register: the reverse crawl from its next-value node (Sec. 5.1)
+    for (size_t r = 0; r < nl.reg_w.size(); r++) {
+        Fiber f;
+        f.reg = int32_t(r);
+        ++epoch;
+        crawl(f, nl.reg_next[r]);
+        out.push_back(std::move(f));
+    }
+    // one fiber per memory with write ports: all its ports' cones together,
+    // so one process applies the memory's write records in port order
+    for (size_t m = 0; m < nl.mem_lg.size(); m++) {
+        if (nl.mem_ports[m].empty()) continue;
+        Fiber f;
+        f.mem = int32_t(m);
+        ++epoch;
+        for (int32_t p : nl.mem_ports[m]) {
+            crawl(f, nl.wports[p].en);
+            crawl(f, nl.wports[p].addr);
+            crawl(f, nl.wports[p].data);
+        }
+        out.push_back(std::move(f));
+    }
+    for (auto& f : out) {
+        std::sort(f.nodes.begin(), f.nodes.end());
+        uint64_t c = sink_cost(nl, f);
+        for (int32_t i : f.nodes) c += node_cost(nl, i);
+        f.cost = c;
+    }
+}
+
+uint64_t union_cost(const Netlist& nl, const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+    uint64_t c = 0;
+    size_t i = 0, j = 0;
+    while (i < a.size() || j < b.size()) {
+        int32_t x;
+        if (j >= b.size() || (i < a.size() && a[i] < b[j])) x = a[i++];
+        else if (i >= a.size() || b[j] < a[i]) x = b[j++];
+        else { x = a[i]; i++; j++; }
+        c += node_cost(nl, x);
+    }
+    return c;
+}
+
+uint64_t inter_cost(const Netlist& nl, const std::vector<int32_t>& a, const std::vector<int32_t>& b) {
+    uint64_t c = 0;
+    size_t i = 0, j = 0;
+    while (i < a.size() && j < b.size()) {
+        if (a[i] < b[j]) i++;
+        else if (b[j] < a[i]) j++;
+        else { c += node_cost(nl, a[i]); i++; j++; }
+    }
+    return c;
+}
+
+// ------------------------------------------------------------------------
+// Submodular load balancing (paper Sec. 5.1)
+// ------------------------------------------------------------------------
+namespace {
+
+struct Proc {
+    std::vector<int32_t> nodes;    // sorted union of the fibers' nodes
+    std::vector<int32_t> fibers;
+    uint64_t sink = 0;             // stores/records/commits of its fibers
+    uint64_t cost = 0;             // tau = sum of node costs (deduplicated) + sinks
+    uint64_t mem = 0;              // data memory: registers touched and arrays read (bytes)
+    bool alive = true;
+};
+
+struct Slb {
+    const Netlist& nl;
+    const PartitionConfig& cfg;
+    std::vector<Fiber>& fib;
+    std::vector<Proc> P;
+    std::vector<int32_t> proc_of_fiber;
+    std::vector<int32_t> writer_fiber;              // register -> fiber writing it
+    std::vector<std::vector<int32_t>> reader_fibers;  // register -> fibers reading it
+    std::vector<std::vector<int32_t>> reads_of_fiber; // fiber -> registers read
+
+    Slb(const Netlist& n, const PartitionConfig& c, std::vector<Fiber>& f) : nl(n), cfg(c), fib(f) {}
+
+    uint64_t node_set_cost(const std::vector<int32_t>& nodes) const {
+        uint64_t c = 0;
+        for (int32_t i : nodes) c += node_cost(nl, i);
+        return c;
+    }
+
+    uint64_t data_mem(const std::vector<int32_t>& nodes, const std::vector<int32_t>& fibers) const {
+        uint64_t m = 8 * fibers.size();
+        std::unordered_set<int32_t> arrays;
+        for (int32_t i : nodes) {
+            const Node& d = nl.nodes[i];
+            if (d.op == OP_REG) m += 8;
+            if (d.op == OP_MEMRD) arrays.insert(d.a);
+        }
+        for (int32_t f : fibers)
+            if (fib[f].mem >= 0) arrays.insert(fib[f].mem);
+        for (int32_t a : arrays) m += 8ULL << nl.mem_lg[a];
+        return m;
+    }
+
+    void init() {
+        const size_t F = fib.size();
+        writer_fiber.assign(nl.reg_w.size(), -1);
+        reader_fibers.assign(nl.reg_w.size(), {});
+        reads_of_fiber.assign(F, {});
+        for (size_t f = 0; f < F; f++) {
+            if (fib[f].reg >= 0) writer_fiber[fib[f].reg] = int32_t(f);
+            for (int32_t i : fib[f].nodes)
+                if (nl.nodes[i].op == OP_REG) {
+                    reader_fibers[nl.nodes[i].a].push_back(int32_t(f));
+                    reads_of_fiber[f].push_back(nl.nodes[i].a);
+                }
+        }
+        P.resize(F);
+        proc_of_fiber.resize(F);
+        for (size_t f = 0; f < F; f++) {
+            P[f].nodes = fib[f].nodes;
+            P[f].fibers = {int32_t(f)};
+            P[f].sink = sink_cost(nl, fib[f]);
+            P[f].cost = fib[f].cost;
+            P[f].mem = data_mem(P[f].nodes, P[f].fibers);
+            proc_of_fiber[f] = int32_t(f);
+        }
+    }
+
+    void merge_into(int32_t p, int32_t q) {   // q is absorbed by p
+        std::vector<int32_t> u;
+        u.reserve(P[p].nodes.size() + P[q].nodes.size());
+        std::set_union(P[p].nodes.begin(), P[p].nodes.end(), P[q].nodes.begin(), P[q].nodes.end(),
+                       std::back_inserter(u));
+        P[p].nodes.swap(u);
+        for (int32_t f : P[q].fibers) {
+            P[p].fibers.push_back(f);
+            proc_of_fiber[f] = p;
+        }
+        P[p].sink += P[q].sink;
+        P[p].cost = node_set_cost(P[p].nodes) + P[p].sink;
+        P[p].mem = data_mem(P[p].nodes, P[p].fibers);
+        P[q].alive = false;
+        P[q].nodes.clear();
+        P[q].nodes.shrink_to_fit();
+        P[q].fibers.clear();
+    }
+
+    // processes that read a register p writes or write a register p reads
+    void partners(int32_t p, std::vector<int32_t>& out) {
+        out.clear();
+        std::unordered_set<int32_t> seen;
+        auto add = [&](int32_t q) {
+            if (q != p && P[q].alive && seen.insert(q).second) out.push_back(q);
+        };
+        for (int32_t f : P[p].fibers) {
+            for (int32_t r : reads_of_fiber[f]) {
+                if (writer_fiber[r] >= 0) add(proc_of_fiber[writer_fiber[r]]);
+                if (out.size() >= cfg.cand_cap) return;
+            }
+        }
+        for (int32_t f : P[p].fibers) {
+            if (fib[f].reg < 0) continue;
+            for (int32_t g : reader_fibers[fib[f].reg]) {
+                add(proc_of_fiber[g]);
+                if (out.size() >= cfg.cand_cap) return;
+            }
+        }
+    }
+
+    bool mem_ok(int32_t p, int32_t q) const {
+        if (!cfg.mem_budget_bytes) return true;
+        std::vector<int32_t> u;
+        std::set_union(P[p].nodes.begin(), P[p].nodes.end(), P[q].nodes.begin(), P[q].nodes.end(),
+                       std::back_inserter(u));
+        std::vector<int32_t> fs(P[p].fibers);
+        fs.insert(fs.end(), P[q].fibers.begin(), P[q].fibers.end());
+        return data_mem(u, fs) <= cfg.mem_budget_bytes;
+    }
+
+    // Stage 1: fibers that touch the same very large array are merged up front
+    // so no process later needs several large arrays (Sec. 5.1, footnote).
+    void stage1() {
+        std::vector<std::vector<int32_t>> users(nl.mem_lg.size());
+        for (size_t f = 0; f < fib.size(); f++) {
+            std::unordered_set<int32_t> arrays;
+            for (int32_t i : fib[f].nodes)
+                if (nl.nodes[i].op == OP_MEMRD) arrays.insert(nl.nodes[i].a);
+            if (fib[f].mem >= 0) arrays.insert(fib[f].mem);
+            for (int32_t a : arrays) users[a].push_back(int32_t(f));
+        }
+        for (size_t m = 0; m < users.size(); m++) {
+            uint64_t bytes = (uint64_t(nl.mem_w[m] + 7) / 8) << nl.mem_lg[m];
+            if (bytes < cfg.big_array_bytes || users[m].size() < 2) continue;
+            int32_t p = proc_of_fiber[users[m][0]];
+            for (size_t k = 1; k < users[m].size(); k++) {
+                int32_t q = proc_of_fiber[users[m][k]];
+                if (q != p) merge_into(p, q);
+            }
+        }
+    }
+
+    size_t alive_count() const {
+        size_t n = 0;
+        for (auto& p : P) n += p.alive;
+        return n;
+    }
+
+    // Stage 3: conservative merge.  Repeatedly take the cheapest process and
+    // merge it with a process it communicates with, if the merged cost does
+    // not exceed the current worst cost and memory fits; otherwise try the
+    // two cheapest; otherwise skip it (Sec. 5.1).  Among partners, take the
+    // one sharing the most work, then the cheapest, then the lowest id.
+    void stage3(size_t target) {
+        using E = std::pair<uint64_t, int32_t>;
+        std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
+        uint64_t worst = 0;
+        for (size_t p = 0; p < P.size(); p++)
+            if (P[p].alive) {
+                heap.push({P[p].cost, int32_t(p)});
+                worst = std::max(worst, P[p].cost);
+            }
+        size_t count = alive_count();
+        std::vector<uint8_t> done(P.size(), 0);
+        std::vector<int32_t> cand;
+        auto valid = [&](const E& e) { return P[e.second].alive && !done[e.second] && P[e.second].cost == e.first; };
+        while (count > target && !heap.empty()) {
+            E top = heap.top();
+            heap.pop();
+            if (!valid(top)) continue;
+            int32_t p = top.second;
+            partners(p, cand);
+            int32_t best = -1;
+            uint64_t best_shared = 0, best_cost = 0;
+            for (int32_t q : cand) {
+                uint64_t shared = inter_cost(nl, P[p].nodes, P[q].nodes);
+                uint64_t merged = P[p].cost + P[q].cost - shared;
+                if (merged > worst || !mem_ok(p, q)) continue;
+                if (best < 0 || shared > best_shared || (shared == best_shared && (P[q].cost < best_cost ||
+                                                        (P[q].cost == best_cost && q < best)))) {
+                    best = q;
+                    best_shared = shared;
+                    best_cost = P[q].cost;
+                }
+            }
+            if (best < 0) {
+                // the two cheapest: p and the next valid heap entry
+                while (!heap.empty() && !valid(heap.top())) heap.pop();
+                if (!heap.empty()) {
+                    int32_t q = heap.top().second;
+                    uint64_t merged = P[p].cost + P[q].cost - inter_cost(nl, P[p].nodes, P[q].nodes);
+                    if (merged <= worst && mem_ok(p, q)) best = q;
+                }
+            }
+            if (best < 0) {
+                done[p] = 1;
+                continue;
+            }
+            merge_into(p, best);
+            heap.push({P[p].cost, p});
+            count--;
+        }
+    }
+
+    // Stage 4: relaxed merge when stage 3 misses the target: the remaining
+    // processes, most expensive first, each go to the bin whose merged cost
+    // is lowest among the cheapest bins and the bins it communicates with
+    // (the worst cost may grow).  Fails if memory cannot fit.
+    int stage4(size_t target, std::string& err) {
+        std::vector<int32_t> order;
+        for (size_t p = 0; p < P.size(); p++)
+            if (P[p].alive) order.push_back(int32_t(p));
+        if (order.size() <= target) return SIM_OK;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return P[a].cost > P[b].cost; });
+        // the first `target` processes seed the bins
+        std::vector<int32_t> bins(order.begin(), order.begin() + target);
+        std::vector<int32_t> bin_of_proc(P.size(), -1);
+        for (size_t i = 0; i < bins.size(); i++) bin_of_proc[bins[i]] = int32_t(i);
+        using E = std::pair<uint64_t, int32_t>;
+        std::priority_queue<E, std::vector<E>, std::greater<E>> heap;
+        for (size_t i = 0; i < bins.size(); i++) heap.push({P[bins[i]].cost, int32_t(i)});
+        std::vector<int32_t> cand, part;
+        for (size_t k = target; k < order.size(); k++) {
+            int32_t p = order[k];
+            cand.clear();
+            std::vector<E> popped;
+            while (!heap.empty() && popped.size() < 8) {
+                E e = heap.top();
+                heap.pop();
+                if (P[bins[e.second]].cost != e.first) continue;
+                popped.push_back(e);
+                cand.push_back(e.second);
+            }
+            for (auto& e : popped) heap.push(e);
+            partners(p, part);
+            for (int32_t q : part)
+                if (bin_of_proc[q] >= 0) cand.push_back(bin_of_proc[q]);
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            int32_t best = -1;
+            uint64_t best_merged = 0;
+            for (int32_t b : cand) {
+                int32_t q = bins[b];
+                if (!mem_ok(q, p)) continue;
+                uint64_t merged = P[p].cost + P[q].cost - inter_cost(nl, P[p].nodes, P[q].nodes);
+                if (best < 0 || merged < best_merged || (merged == best_merged && P[q].cost < P[bins[best]].cost)) {
+                    best = b;
+                    best_merged = merged;
+                }
+            }
+            if (best < 0) {
+                err = "a process does not fit the per-process memory budget";
+                return SIM_ERR_CAPACITY;
+            }
+            merge_into(bins[best], p);
+            heap.push({P[bins[best]].cost, best});
+        }
+        return SIM_OK;
+    }
+
+    void random_partition(size_t target, uint32_t seed) {
+        std::mt19937 rng(seed);
+        target = std::max<size_t>(1, std::min(target ? target : 64, P.size()));
+        std::vector<int32_t> bins(target, -1);
+        std::vector<int32_t> order(P.size());
+        std::iota(order.begin(), order.end(), 0);
+        std::shuffle(order.begin(), order.end(), rng);
+        for (size_t k = 0; k < order.size(); k++) {
+            size_t b = k < target ? k : rng() % target;
+            if (bins[b] < 0) bins[b] = order[k];
+            else merge_into(bins[b], order[k]);
+        }
+    }
+};
+
+}  // namespace
+
+int partition(const Netlist& nl, const PartitionConfig& cfg, Partition& out, std::string& err) {
+    extract_fibers(nl, out.fibers);
+    out.fiber_cost_sum = out.fiber_cost_max = 0;
+    for (auto& f : out.fibers) {
+        out.fiber_cost_sum += f.cost;
+        out.fiber_cost_max = std::max(out.fiber_cost_max, f.cost);
+    }
+    Slb s(nl, cfg, out.fibers);
+    s.init();
+    if (cfg.random_seed) {
+        s.random_partition(cfg.target, cfg.random_seed);
+    } else {
+        s.stage1();
+        size_t target = cfg.target ? cfg.target : s.P.size();
+        if (cfg.stage3) s.stage3(target);
+        int rc = s.stage4(target, err);
+        if (rc) return rc;
+    }
+    out.procs.clear();
+    out.proc_cost.clear();
+    out.proc_cost_sum = out.proc_cost_max = 0;
+    for (auto& p : s.P) {
+        if (!p.alive) continue;
+        std::vector<int32_t> fs = p.fibers;
+        std::sort(fs.begin(), fs.end());
+        out.procs.push_back(std::move(fs));
+        out.proc_cost.push_back(p.cost);
+        out.proc_cost_sum += p.cost;
+        out.proc_cost_max = std::max(out.proc_cost_max, p.cost);
+    }
+    // cut: register words a process reads but another process writes
+    std::vector<int32_t> proc_of_reg(nl.reg_w.size(), -1);
+    for (size_t p = 0; p < out.procs.size(); p++)
+        for (int32_t f : out.procs[p])
+            if (out.fibers[f].reg >= 0) proc_of_reg[out.fibers[f].reg] = int32_t(p);
+    out.cut_words = 0;
+    for (size_t p = 0; p < out.procs.size(); p++) {
+        std::unordered_set<int32_t> regs;
+        for (int32_t f : out.procs[p])
+            for (int32_t i : out.fibers[f].nodes)
+                if (nl.nodes[i].op == OP_REG && proc_of_reg[nl.nodes[i].a] != int32_t(p)) regs.insert(nl.nodes[i].a);
+        out.cut_words += regs.size();
+    }
+    return SIM_OK;
+}
+
+// ------------------------------------------------------------------------
+// Lowering
+// ------------------------------------------------------------------------
+RegLayout reg_layout(const Netlist& nl) {
+    RegLayout L;
+    L.cls.resize(nl.reg_w.size());
+    L.idx.resize(nl.reg_w.size());
+    for (size_t r = 0; r < nl.reg_w.size(); r++) {
+        RegClass c = reg_class(nl.reg_w[r]);
+        L.cls[r] = c;
+        L.idx[r] = L.count[c]++;
+    }
+    return L;
+}
+
+namespace {
+
+// One schedule item: a node's value, or a sink action.
+struct Item {
+    int kind;          // 0 = node, 1 = register store, 2 = write record, 3 = memory commit
+    int32_t id;        // node id / register / port / memory
+    int level;
+    uint8_t op;        // for sorting within a level
+};
+
+constexpr uint16_t kNoSlot = 0xffff;
+
+// Slot allocation over a sequence of steps.  Each step defines some values
+// and uses some; a value's slot is released after its last use.  With
+// `free_before_def` a step's operands whose last use is this step are
+// released before its own definitions (sequential execution); otherwise only
+// after the step completes (32 lanes run the step at once).
+struct SlotAlloc {
+    std::vector<uint16_t> free_list;
+    uint32_t next = 0;
+    uint16_t get() {
+        if (!free_list.empty()) {
+            uint16_t s = free_list.back();
+            free_list.pop_back();
+            return s;
+        }
+        return uint16_t(next++);
+    }
+    void put(uint16_t s) { free_list.push_back(s); }
+};
+
+}  // namespace
+
+int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& err) {
+    RegLayout L = reg_layout(nl);
+    const size_t NP = part.procs.size();
+    out = Lowered();
+    out.s_off.resize(NP);
+    out.s_len.resize(NP);
+    out.s_slots.resize(NP);
+    out.b_off.resize(NP);
+    out.b_len.resize(NP);
+    out.b_slots.resize(NP);
+    out.commit_proc.assign(nl.mem_lg.size(), -1);
+    std::vector<int32_t> local(nl.nodes.size(), -1);
+
+    for (size_t p = 0; p < NP; p++) {
+        // node set: union of the process's fibers
+        std::vector<int32_t> nodes;
+        for (int32_t f : part.procs[p]) nodes.insert(nodes.end(), part.fibers[f].nodes.begin(), part.fibers[f].nodes.end());
+        std::sort(nodes.begin(), nodes.end());
+        nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+        for (size_t i = 0; i < nodes.size(); i++) local[nodes[i]] = int32_t(i);
+
+        std::vector<Item> items;
+        items.reserve(nodes.size() + part.procs[p].size() * 2);
+        for (int32_t id : nodes) items.push_back({0, id, nl.level[id], nl.nodes[id].op});
+        for (int32_t f : part.procs[p]) {
+            const Fiber& fb = part.fibers[f];
+            if (fb.reg >= 0) {
+                items.push_back({1, fb.reg, nl.level[nl.reg_next[fb.reg]] + 1, 255});
+            } else {
+                out.commit_proc[fb.mem] = int32_t(p);
+                items.push_back({3, fb.mem, 0, 254});
+                for (int32_t port : nl.mem_ports[fb.mem]) {
+                    const WPort& w = nl.wports[port];
+                    int lv = std::max({nl.level[w.en], nl.level[w.addr], nl.level[w.data]}) + 1;
+                    items.push_back({2, port, lv, 253});
+                }
+            }
+        }
+        // steps: by level, then operator kind (less divergence in a step), then id
+        std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+            if (a.level != b.level) return a.level < b.level;
+            if (a.op != b.op) return a.op < b.op;
+            if (a.kind != b.kind) return a.kind < b.kind;
+            return a.id < b.id;
+        });
+        // bundle index of each item (32 per step, never mixing levels)
+        std::vector<uint32_t> bundle(items.size());
+        uint32_t nb = 0;
+        {
+            int cur_level = -1;
+            uint32_t fill = 0;
+            for (size_t i = 0; i < items.size(); i++) {
+                if (items[i].level != cur_level || fill == 32) {
+                    nb++;
+                    fill = 0;
+                    cur_level = items[i].level;
+                }
+                bundle[i] = nb - 1;
+                fill++;
+            }
+        }
+        // last use (bundle and sequential position) of each local value
+        std::vector<int32_t> last_b(nodes.size(), -1);
+        auto use = [&](int32_t node, size_t i) {
+            int32_t l = local[node];
+            last_b[l] = std::max<int32_t>(last_b[l], int32_t(bundle[i]));
+        };
+        auto operands = [&](const Item& it, auto&& f) {
+            if (it.kind == 0) {
+                const Node& d = nl.nodes[it.id];
+                switch (d.op) {
+                case OP_INPUT: case OP_REG: case OP_CONST: break;
+                case OP_MEMRD: f(d.b); break;
+                case OP_SLICE: f(d.a); break;
+                case OP_MUX: f(d.a); f(d.b); f(d.c); break;
+                default: f(d.a); f(d.b);
+                }
+            } else if (it.kind == 1) {
+                f(nl.reg_next[it.id]);
+            } else if (it.kind == 2) {
+                const WPort& w = nl.wports[it.id];
+                f(w.en); f(w.addr); f(w.data);
+            }
+        };
+        for (size_t i = 0; i < items.size(); i++) operands(items[i], [&](int32_t o) { use(o, i); });
+
+        auto make_ins = [&](const Item& it, const std::vector<uint16_t>& slot) {
+            DIns d{};
+            d.op = D_NOP;
+            auto S = [&](int32_t node) { return slot[local[node]]; };
+            if (it.kind == 0) {
+                const Node& n = nl.nodes[it.id];
+                d.w = n.w;
+                d.dst = slot[local[it.id]];
+                switch (n.op) {
+                case OP_INPUT: d.op = D_LDI; d.imm = uint32_t(n.a); break;
+                case OP_REG:
+                    d.op = D_LDR;
+                    d.c = L.cls[n.a];
+                    d.b = uint16_t(L.idx[n.a] & 0xffff);
+                    d.x = uint16_t(L.idx[n.a] >> 16);
+                    d.imm = uint32_t(n.a);
+                    break;
+                case OP_CONST:
+                    d.op = D_CONST;
+                    d.imm = uint32_t(n.k);
+                    d.a = uint16_t(n.k >> 32);
+                    d.b = uint16_t(n.k >> 48);
+                    break;
+                case OP_MEMRD: d.op = D_MEMRD; d.a = S(n.b); d.imm = uint32_t(n.a); break;
+                case OP_SLICE: d.op = D_SLICE; d.a = S(n.a); d.x = uint16_t(n.b); break;
+                case OP_CONCAT: d.op = D_CONCAT; d.a = S(n.a); d.b = S(n.b); d.x = nl.nodes[n.b].w; break;
+                case OP_MUX: d.op = D_MUX; d.a = S(n.a); d.b = S(n.b); d.c = S(n.c); break;
+                default:
+                    d.op = uint8_t(D_ADD + (n.op - OP_ADD));
+                    d.a = S(n.a);
+                    d.b = S(n.b);
+                }
+            } else if (it.kind == 1) {
+                int32_t r = it.id;
+                d.op = D_STR;
+                d.w = nl.reg_w[r];
+                d.a = S(nl.reg_next[r]);
+                d.c = L.cls[r];
+                d.b = uint16_t(L.idx[r] & 0xffff);
+                d.x = uint16_t(L.idx[r] >> 16);
+                d.imm = uint32_t(r);
+            } else if (it.kind == 2) {
+                const WPort& w = nl.wports[it.id];
+                d.op = D_WREC;
+                d.a = S(w.en);
+                d.b = S(w.addr);
+                d.c = S(w.data);
+                d.w = nl.mem_w[w.mem];
+                d.x = nl.mem_lg[w.mem];
+                d.imm = uint32_t(it.id);
+            } else {
+                d.op = D_COMMIT;
+                d.imm = uint32_t(it.id);
+            }
+            return d;
+        };
+
+        // ---- LANE_OP: 32-wide bundles, slots freed after a bundle completes
+        {
+            std::vector<uint16_t> slot(nodes.size(), kNoSlot);
+            SlotAlloc A;
+            std::vector<std::vector<uint16_t>> release(nb + 1);
+            size_t i = 0;
+            out.s_off[p] = uint32_t(out.s_ins.size() / 32);
+            for (uint32_t b = 0; b < nb; b++) {
+                for (uint16_t s : release[b]) A.put(s);
+                size_t base = out.s_ins.size();
+                out.s_ins.resize(base + 32, DIns{});
+                int lane = 0;
+                for (; i < items.size() && bundle[i] == b; i++, lane++) {
+                    const Item& it = items[i];
+                    if (it.kind == 0) {
+                        int32_t l = local[it.id];
+                        slot[l] = A.get();
+                        if (last_b[l] >= 0) release[last_b[l] + 1].push_back(slot[l]);
+                        else release[b + 1].push_back(slot[l]);
+                    }
+                    out.s_ins[base + lane] = make_ins(it, slot);
+                }
+            }
+            out.s_len[p] = nb;
+            out.s_slots[p] = std::max<uint32_t>(1, A.next);
+            if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
+        }
+        // ---- LANE_INST: sequential list in depth-first post-order from each
+        // sink (a value is computed right before its first consumer, which
+        // keeps few values live), operand slots reusable by the result
+        {
+            std::vector<int32_t> item_of_node(nodes.size(), -1);
+            for (size_t i = 0; i < items.size(); i++)
+                if (items[i].kind == 0) item_of_node[local[items[i].id]] = int32_t(i);
+            std::vector<int32_t> seq;
+            seq.reserve(items.size());
+            std::vector<uint8_t> emitted(items.size(), 0);
+            std::vector<std::pair<int32_t, int>> stack;   // (item, next operand to visit)
+            auto ops_of = [&](int32_t it, std::vector<int32_t>& v) {
+                v.clear();
+                operands(items[it], [&](int32_t o) { v.push_back(item_of_node[local[o]]); });
+            };
+            std::vector<int32_t> tmp;
+            auto visit = [&](int32_t root) {
+                if (emitted[root]) return;
+                stack.push_back({root, 0});
+                while (!stack.empty()) {
+                    auto& [it, k] = stack.back();
+                    ops_of(it, tmp);
+                    if (k < int(tmp.size())) {
+                        int32_t o = tmp[k++];
+                        if (!emitted[o]) stack.push_back({o, 0});
+                        continue;
+                    }
+                    int32_t done_it = it;
+                    stack.pop_back();
+                    if (!emitted[done_it]) {
+                        emitted[done_it] = 1;
+                        seq.push_back(done_it);
+                    }
+                }
+            };
+            for (size_t i = 0; i < items.size(); i++)      // commits first
+                if (items[i].kind == 3) visit(int32_t(i));
+            for (size_t i = 0; i < items.size(); i++)      // then every sink's cone
+                if (items[i].kind == 1 || items[i].kind == 2) visit(int32_t(i));
+            // last sequential use of each value in this order
+            std::vector<int32_t> last_seq(nodes.size(), -1);
+            for (size_t k = 0; k < seq.size(); k++)
+                operands(items[seq[k]], [&](int32_t o) { last_seq[local[o]] = int32_t(k); });
+            std::vector<uint16_t> slot(nodes.size(), kNoSlot);
+            SlotAlloc A;
+            out.b_off[p] = uint32_t(out.b_ins.size());
+            std::vector<uint16_t> freed;
+            for (size_t k = 0; k < seq.size(); k++) {
+                const Item& it = items[seq[k]];
+                freed.clear();
+                operands(it, [&](int32_t o) {
+                    int32_t l = local[o];
+                    if (last_seq[l] == int32_t(k)) freed.push_back(slot[l]);
+                });
+                std::sort(freed.begin(), freed.end());
+                freed.erase(std::unique(freed.begin(), freed.end()), freed.end());
+                DIns d;
+                if (it.kind == 0) {
+                    // operands are read before the result is written, so the
+                    // result may take a slot freed by this very instruction
+                    int32_t l = local[it.id];
+                    for (uint16_t s : freed) A.put(s);
+                    slot[l] = A.get();
+                    d = make_ins(it, slot);
+                    if (last_seq[l] < 0) A.put(slot[l]);
+                } else {
+                    d = make_ins(it, slot);
+                    for (uint16_t s : freed) A.put(s);
+                }
+                out.b_ins.push_back(d);
+            }
+            out.b_len[p] = uint32_t(seq.size());
+            out.b_slots[p] = std::max<uint32_t>(1, A.next);
+            if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
+        }
+        out.max_bundles = std::max(out.max_bundles, out.s_len[p]);
+        out.max_s_slots = std::max(out.max_s_slots, out.s_slots[p]);
+        out.max_b_slots = std::max(out.max_b_slots, out.b_slots[p]);
+        for (int32_t id : nodes) local[id] = -1;
+    }
+    return SIM_OK;
+}
+
+}  // namespace rtl

@@ -1,0 +1,473 @@
+// kernels.cu -- sm_103a kernels of the BSP simulator.
+//
+// One simulated clock cycle (paper Sec. 3.2): every process reads *current*
+// register values (buffer t&1), evaluates its fibers' nodes in dependence
+// order, and writes *next* values (buffer (t+1)&1) and memory write records;
+// then a barrier.  Double-buffered state makes the paper's two barriers per
+// cycle (compute, exchange) one: next values are written straight into the
+// buffer the consumers read after the barrier, so the exchange is the store
+// itself (HBM/L2 between processes).  Memory writes travel as (en, addr,
+// data) records, never whole arrays (differential exchange, Sec. 5.2): the
+// records of cycle t are applied to the array by its owning process during
+// cycle t+1, while readers in cycle t+1 forward from them, so every read sees
+// the array as of the clock edge.
+//
+// Two lane mappings share one bytecode:
+//   LANE_OP   warp = (process, instance); lanes run up to 32 independent
+//             nodes of one schedule step, __syncwarp between steps.
+//   LANE_INST warp = (process, 32 instances); lane = instance, uniform
+//             control flow, instance-minor state (coalesced 128/256 B rows),
+//             1-bit registers packed 32 instances per word with __ballot_sync.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/sim.h"
+#include "device.hpp"
+
+namespace rtl {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    // SplitMix64 output function (Steele, Lea, Flood 2014)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t wmask(uint32_t w) { return ~0ULL >> (64 - w); }   // w in 1..64
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *(volatile const int32_t*)p; }
+
+__device__ __forceinline__ uint4 ld_ins(const DIns* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+
+// Grid-wide barrier: arrival counter plus generation word.  Every wait is
+// bounded: past `timeout_ns`, or once another CTA has recorded an error, the
+// CTA records SIM_ERR_TIMEOUT (first error wins) and returns false.
+__device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeout_ns, int32_t* err, bool skip) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        if (!skip) {
+            uint32_t arrived = atomicAdd(&bar[0], 1u);
+            if (arrived == gridDim.x - 1) {
+                atomicExch(&bar[0], 0u);
+                __threadfence();
+                atomicExch(&bar[1], gen + 1);
+            }
+        }
+        uint64_t start = globaltimer_ns();
+        while (ld_acquire(&bar[1]) == gen) {
+            if (ld_volatile(err) != 0) { ok = 0; break; }
+            if (globaltimer_ns() - start > timeout_ns) {
+                atomicCAS(err, 0, SIM_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        gen++;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// Instruction semantics (shared by both lane mappings)
+// ---------------------------------------------------------------------------
+struct Dec {
+    uint32_t op, w, dst, a, b, c, x, imm;
+};
+
+__device__ __forceinline__ Dec decode(uint4 r) {
+    Dec d;
+    d.op = r.x & 0xff;
+    d.w = (r.x >> 8) & 0xff;
+    d.dst = r.x >> 16;
+    d.a = r.y & 0xffff;
+    d.b = r.y >> 16;
+    d.c = r.z & 0xffff;
+    d.x = r.z >> 16;
+    d.imm = r.w;
+    return d;
+}
+
+__device__ __forceinline__ uint64_t alu(uint32_t op, uint64_t a, uint64_t b, uint64_t c, uint32_t x) {
+    switch (op) {
+    case D_ADD: return a + b;
+    case D_SUB: return a - b;
+    case D_MUL: return a * b;
+    case D_AND: return a & b;
+    case D_OR: return a | b;
+    case D_XOR: return a ^ b;
+    case D_SHL: return b >= 64 ? 0 : a << b;
+    case D_SHR: return b >= 64 ? 0 : a >> b;
+    case D_EQ: return a == b ? 1 : 0;
+    case D_LT: return a < b ? 1 : 0;
+    case D_MUX: return a != 0 ? b : c;
+    case D_SLICE: return a >> x;           // lo < 64 (checked at load)
+    case D_CONCAT: return (a << x) | b;    // width(b) < 64 (checked at load)
+    default: return 0;
+    }
+}
+
+__device__ __forceinline__ uint64_t load_reg(const DevState& S, uint32_t par, uint32_t cls, uint32_t idx, uint32_t inst) {
+    if (cls == RC_W64) return S.w64[par][(uint64_t)idx * S.I + inst];
+    if (cls == RC_W32) return S.w32[par][(uint64_t)idx * S.I + inst];
+    uint32_t word = S.bits[par][(uint64_t)idx * S.bit_stride + inst / S.pack];
+    return (word >> (inst % S.pack)) & 1u;
+}
+
+__device__ __forceinline__ uint64_t stimulus(const DevProg& P, const DevState& S, uint64_t key, uint32_t k, uint32_t inst,
+                                             uint64_t t, uint32_t w) {
+    if (S.any_hold) {
+        uint64_t j = (uint64_t)k * S.I + inst;
+        if (S.hold_flag[j]) return S.hold_val[j] & wmask(w);
+    }
+    return mix64(key + (t * P.n_in + k + 1) * kGamma) & wmask(w);
+}
+
+__device__ __forceinline__ uint64_t mem_hash(uint32_t m, uint64_t a) {
+    return ((1ULL << 40) + ((uint64_t)m << 24) + a) * kGamma + 1ULL;
+}
+
+// Read memory m at addr for inst as of the clock edge: the array plus the
+// pending write records of the previous cycle (highest port wins).
+__device__ __forceinline__ uint64_t mem_read(const DevProg& P, const DevState& S, uint32_t m, uint64_t addr, uint32_t inst,
+                                             uint32_t prev, bool pending) {
+    uint64_t v = S.mem[P.mem_base[m] + addr * S.I + inst];
+    if (pending) {
+        for (uint32_t j = P.mport_off[m]; j < P.mport_off[m + 1]; j++) {
+            const uint64_t* r = S.rec[prev] + ((uint64_t)P.mport_id[j] * S.I + inst) * 2;
+            uint64_t ea = r[0];
+            if ((ea >> 63) && (ea & ~(1ULL << 63)) == addr) v = r[1];
+        }
+    }
+    return v;
+}
+
+// Apply the previous cycle's write records of memory m for one instance
+// (ascending port order) and return the change of the memory digest.
+__device__ __forceinline__ uint64_t mem_commit(const DevProg& P, const DevState& S, uint32_t m, uint32_t inst, uint32_t prev,
+                                               bool digest) {
+    uint64_t delta = 0;
+    for (uint32_t j = P.mport_off[m]; j < P.mport_off[m + 1]; j++) {
+        const uint64_t* r = S.rec[prev] + ((uint64_t)P.mport_id[j] * S.I + inst) * 2;
+        uint64_t ea = r[0];
+        if (ea >> 63) {
+            uint64_t addr = ea & ~(1ULL << 63);
+            uint64_t* cell = S.mem + P.mem_base[m] + addr * S.I + inst;
+            uint64_t old = *cell, nv = r[1];
+            *cell = nv;
+            if (digest) delta += mix64(mem_hash(m, addr) ^ nv) - mix64(mem_hash(m, addr) ^ old);
+        }
+    }
+    return delta;
+}
+
+__device__ __forceinline__ void ring_add(const DevState& S, uint64_t t, int32_t col, uint64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(S.ring + (t % S.ring_cap) * S.n_tracked + col),
+              (unsigned long long)v);
+}
+
+// Memory part of the digest at cycle t (records of t-1 just applied).
+__device__ __forceinline__ void mem_digest_update(const DevState& S, uint32_t m, uint32_t inst, uint64_t t, uint64_t delta) {
+    int32_t col = S.track[inst];
+    if (col < 0) return;
+    uint64_t* md = S.mem_dig + (uint64_t)m * S.I + inst;
+    uint64_t v = *md + delta;
+    *md = v;
+    ring_add(S, t, col, v);
+}
+
+// ---------------------------------------------------------------------------
+// LANE_INST: one warp, one process, 32 instances (lane = instance).
+// ---------------------------------------------------------------------------
+template <bool DIGEST>
+__device__ void task_lane_inst(const DevProg& P, const DevState& S, uint32_t p, uint32_t g, uint64_t t, bool pending,
+                               uint64_t* __restrict__ sl, uint32_t lane) {
+    const uint32_t inst = g * 32 + lane;
+    const uint32_t par = uint32_t(t & 1), nxt = par ^ 1;
+    const uint64_t key = S.key[inst];
+    const int32_t col = DIGEST ? S.track[inst] : -1;
+    uint64_t dacc = 0;
+    const DIns* ip = P.b_ins + P.b_off[p];
+    const uint32_t n = P.b_len[p];
+#define SL(s) sl[(s) * 32 + lane]
+    for (uint32_t i = 0; i < n; i++) {
+        Dec d = decode(ld_ins(ip + i));
+        switch (d.op) {
+        case D_NOP:
+            break;
+        case D_LDR:
+            SL(d.dst) = load_reg(S, par, d.c, d.b | (d.x << 16), inst);
+            break;
+        case D_LDI:
+            SL(d.dst) = stimulus(P, S, key, d.imm, inst, t, d.w);
+            break;
+        case D_CONST:
+            SL(d.dst) = (uint64_t)d.imm | ((uint64_t)d.a << 32) | ((uint64_t)d.b << 48);
+            break;
+        case D_MEMRD: {
+            uint64_t addr = SL(d.a) & ((1ULL << P.mem_lg[d.imm]) - 1);
+            SL(d.dst) = mem_read(P, S, d.imm, addr, inst, nxt, pending);
+            break;
+        }
+        case D_STR: {
+            uint64_t v = SL(d.a) & wmask(d.w);
+            uint32_t idx = d.b | (d.x << 16);
+            if (d.c == RC_W64) {
+                S.w64[nxt][(uint64_t)idx * S.I + inst] = v;
+            } else if (d.c == RC_W32) {
+                S.w32[nxt][(uint64_t)idx * S.I + inst] = uint32_t(v);
+            } else {
+                uint32_t word = __ballot_sync(0xffffffffu, v & 1);
+                if (lane == 0) S.bits[nxt][(uint64_t)idx * S.bit_stride + g] = word;
+            }
+            if (DIGEST && col >= 0) dacc += mix64(((uint64_t)d.imm * kGamma + 1ULL) ^ v);
+            break;
+        }
+        case D_WREC: {
+            uint64_t en = SL(d.a) != 0;
+            uint64_t addr = SL(d.b) & ((1ULL << d.x) - 1);
+            uint64_t data = SL(d.c) & wmask(d.w);
+            uint64_t* r = S.rec[par] + ((uint64_t)d.imm * S.I + inst) * 2;
+            r[0] = en ? ((1ULL << 63) | addr) : 0;
+            r[1] = data;
+            break;
+        }
+        case D_COMMIT:
+            if (pending) {
+                uint64_t delta = mem_commit(P, S, d.imm, inst, nxt, DIGEST && col >= 0);
+                if (DIGEST) mem_digest_update(S, d.imm, inst, t, delta);
+            }
+            break;
+        case D_MUX:
+            SL(d.dst) = alu(D_MUX, SL(d.a), SL(d.b), SL(d.c), 0) & wmask(d.w);
+            break;
+        default:
+            SL(d.dst) = alu(d.op, SL(d.a), SL(d.b), 0, d.x) & wmask(d.w);
+        }
+    }
+#undef SL
+    if (DIGEST && col >= 0) ring_add(S, t + 1, col, dacc);
+}
+
+// ---------------------------------------------------------------------------
+// LANE_OP: one warp, one process, one instance; lanes run a 32-wide step.
+// ---------------------------------------------------------------------------
+template <bool DIGEST>
+__device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t, bool pending,
+                             uint64_t* __restrict__ sl, uint32_t lane) {
+    const uint32_t par = uint32_t(t & 1), nxt = par ^ 1;
+    const uint64_t key = S.key[inst];
+    const int32_t col = DIGEST ? S.track[inst] : -1;
+    uint64_t dacc = 0;
+    const DIns* bp = P.s_ins + (uint64_t)P.s_off[p] * 32 + lane;
+    const uint32_t nb = P.s_len[p];
+    uint4 raw = nb ? ld_ins(bp) : make_uint4(0, 0, 0, 0);
+    for (uint32_t b = 0; b < nb; b++) {
+        uint4 next_raw = (b + 1 < nb) ? ld_ins(bp + (uint64_t)(b + 1) * 32) : make_uint4(0, 0, 0, 0);
+        Dec d = decode(raw);
+        switch (d.op) {
+        case D_NOP:
+            break;
+        case D_LDR:
+            sl[d.dst] = load_reg(S, par, d.c, d.b | (d.x << 16), inst);
+            break;
+        case D_LDI:
+            sl[d.dst] = stimulus(P, S, key, d.imm, inst, t, d.w);
+            break;
+        case D_CONST:
+            sl[d.dst] = (uint64_t)d.imm | ((uint64_t)d.a << 32) | ((uint64_t)d.b << 48);
+            break;
+        case D_MEMRD: {
+            uint64_t addr = sl[d.a] & ((1ULL << P.mem_lg[d.imm]) - 1);
+            sl[d.dst] = mem_read(P, S, d.imm, addr, inst, nxt, pending);
+            break;
+        }
+        case D_STR: {
+            uint64_t v = sl[d.a] & wmask(d.w);
+            uint32_t idx = d.b | (d.x << 16);
+            if (d.c == RC_W64) S.w64[nxt][(uint64_t)idx * S.I + inst] = v;
+            else if (d.c == RC_W32) S.w32[nxt][(uint64_t)idx * S.I + inst] = uint32_t(v);
+            else S.bits[nxt][(uint64_t)idx * S.bit_stride + inst] = uint32_t(v);   // pack == 1
+            if (DIGEST && col >= 0) dacc += mix64(((uint64_t)d.imm * kGamma + 1ULL) ^ v);
+            break;
+        }
+        case D_WREC: {
+            uint64_t en = sl[d.a] != 0;
+            uint64_t addr = sl[d.b] & ((1ULL << d.x) - 1);
+            uint64_t data = sl[d.c] & wmask(d.w);
+            uint64_t* r = S.rec[par] + ((uint64_t)d.imm * S.I + inst) * 2;
+            r[0] = en ? ((1ULL << 63) | addr) : 0;
+            r[1] = data;
+            break;
+        }
+        case D_COMMIT:
+            if (pending) {
+                uint64_t delta = mem_commit(P, S, d.imm, inst, nxt, DIGEST && col >= 0);
+                if (DIGEST) mem_digest_update(S, d.imm, inst, t, delta);
+            }
+            break;
+        case D_MUX:
+            sl[d.dst] = alu(D_MUX, sl[d.a], sl[d.b], sl[d.c], 0) & wmask(d.w);
+            break;
+        default:
+            sl[d.dst] = alu(d.op, sl[d.a], sl[d.b], 0, d.x) & wmask(d.w);
+        }
+        __syncwarp();
+        raw = next_raw;
+    }
+    if (DIGEST && col >= 0) {
+        for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+        if (lane == 0) ring_add(S, t + 1, col, dacc);
+    }
+}
+
+// Apply the last cycle's write records after the final barrier of a launch
+// (or in a launch of its own after per-cycle launches).
+__device__ void final_commit(const DevProg& P, const DevState& S, uint64_t t_end, uint64_t gtid, uint64_t gthreads) {
+    const uint32_t prev = uint32_t((t_end - 1) & 1);
+    const uint64_t total = (uint64_t)P.n_mem * S.I;
+    for (uint64_t e = gtid; e < total; e += gthreads) {
+        uint32_t m = uint32_t(e / S.I), inst = uint32_t(e % S.I);
+        if (P.mport_off[m] == P.mport_off[m + 1]) continue;
+        bool dig = S.ring_cap && S.track[inst] >= 0;
+        uint64_t delta = mem_commit(P, S, m, inst, prev, dig);
+        if (dig) mem_digest_update(S, m, inst, t_end, delta);
+    }
+}
+
+template <int MODE, bool DIGEST>
+__global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchArgs A) {
+    extern __shared__ uint64_t smem[];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t warp = blockIdx.x * A.warps_per_cta + wib;
+    const uint32_t tw = gridDim.x * A.warps_per_cta;
+    uint64_t* sl = smem + (uint64_t)wib * A.slot_words;
+    uint32_t gen = 0;
+    const uint64_t t_base = A.t0_dev ? *A.t0_dev + A.t0 : A.t0;
+    for (uint32_t c = 0; c < A.n; c++) {
+        const uint64_t t = t_base + c;
+        const bool pending = c > 0 || A.pending_first;
+        for (uint32_t task = warp; task < A.n_tasks; task += tw) {
+            uint32_t p = task % P.n_proc, g = task / P.n_proc;
+            if (MODE == SIM_MODE_LANE_INST) task_lane_inst<DIGEST>(P, S, p, g, t, pending, sl, lane);
+            else task_lane_op<DIGEST>(P, S, p, g, t, pending, sl, lane);
+        }
+        if (A.grid_sync) {
+            bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
+            if (!grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip)) return;
+        }
+    }
+    if (A.grid_sync && A.n > 0)
+        final_commit(P, S, t_base + A.n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+}
+
+__global__ void k_commit(DevProg P, DevState S, uint64_t t_end, const uint64_t* t0_dev) {
+    if (t0_dev) t_end += *t0_dev;
+    final_commit(P, S, t_end, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+}
+
+// Advance the device-resident cycle base of a replayed graph chunk.
+__global__ void k_advance(uint64_t* t0_dev, uint64_t n) { *t0_dev += n; }
+
+// Full digest of buffer `par`: registers (part 0) and memory words (part 1),
+// each thread summing a chunk of items for one instance.
+__global__ void k_state_digest(DevProg P, DevState S, uint32_t par, const uint64_t* mem_word_off, uint64_t mem_words,
+                               uint64_t* out, uint32_t n_inst, uint32_t chunk) {
+    uint32_t inst = blockIdx.x * blockDim.x + threadIdx.x;
+    if (inst >= n_inst) return;
+    uint64_t first = (uint64_t)blockIdx.y * chunk;
+    uint64_t items = (uint64_t)P.n_reg + mem_words;
+    uint64_t last = first + chunk < items ? first + chunk : items;
+    uint64_t acc = 0;
+    for (uint64_t j = first; j < last; j++) {
+        if (j < P.n_reg) {
+            uint64_t v = load_reg(S, par, P.reg_cls[j], P.reg_idx[j], inst);
+            acc += mix64((j * kGamma + 1ULL) ^ v);
+        } else {
+            uint64_t w = j - P.n_reg;
+            uint32_t m = 0;
+            while (m + 1 < P.n_mem && mem_word_off[m + 1] <= w) m++;
+            uint64_t a = w - mem_word_off[m];
+            acc += mix64(mem_hash(m, a) ^ S.mem[P.mem_base[m] + a * S.I + inst]);
+        }
+    }
+    atomicAdd(reinterpret_cast<unsigned long long*>(out + inst), (unsigned long long)acc);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers
+// ---------------------------------------------------------------------------
+template <int MODE, bool DIGEST>
+static void* kfun() { return reinterpret_cast<void*>(&k_cycles<MODE, DIGEST>); }
+
+static void* cycles_fn(int mode, bool digest) {
+    if (mode == SIM_MODE_LANE_INST) return digest ? kfun<SIM_MODE_LANE_INST, true>() : kfun<SIM_MODE_LANE_INST, false>();
+    return digest ? kfun<SIM_MODE_LANE_OP, true>() : kfun<SIM_MODE_LANE_OP, false>();
+}
+
+cudaError_t prepare_cycles_kernel(int mode, size_t smem) {
+    cudaError_t e = cudaSuccess;
+    for (int d = 0; d < 2; d++) {
+        e = cudaFuncSetAttribute(cycles_fn(mode, d), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+    }
+    return e;
+}
+
+cudaError_t occupancy_cycles(int mode, int threads, size_t smem, int* blocks_per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, cycles_fn(mode, false), threads, smem);
+}
+
+cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int threads, size_t smem, cudaStream_t st,
+                          const DevProg& P, const DevState& S, const LaunchArgs& A) {
+    void* f = cycles_fn(mode, digest);
+    DevProg p = P;
+    DevState s = S;
+    LaunchArgs a = A;
+    void* args[] = {&p, &s, &a};
+    if (cooperative) return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, smem, st);
+    return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
+}
+
+cudaError_t launch_commit(int grid, cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t_end,
+                          const uint64_t* t0_dev) {
+    k_commit<<<grid, 256, 0, st>>>(P, S, t_end, t0_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(cudaStream_t st, uint64_t* t0_dev, uint64_t n) {
+    k_advance<<<1, 1, 0, st>>>(t0_dev, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_digest(cudaStream_t st, const DevProg& P, const DevState& S, uint32_t par,
+                                const uint64_t* mem_word_off, uint64_t mem_words, uint64_t* out, uint32_t n_inst) {
+    const uint32_t chunk = 256;
+    uint64_t items = (uint64_t)P.n_reg + mem_words;
+    dim3 grid((n_inst + 127) / 128, uint32_t((items + chunk - 1) / chunk));
+    if (grid.y == 0) return cudaSuccess;
+    k_state_digest<<<grid, 128, 0, st>>>(P, S, par, mem_word_off, mem_words, out, n_inst, chunk);
+    return cudaGetLastError();
+}
+
+}  // namespace rtl

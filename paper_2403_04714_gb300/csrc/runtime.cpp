@@ -1,0 +1,994 @@
+// runtime.cpp -- C ABI of the simulator (include/sim.h): netlist handles,
+// batches of instances in device memory, stepping, peek/poke, digests.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/sim.h"
+#include "compiler.hpp"
+#include "device.hpp"
+
+namespace rtl {
+cudaError_t prepare_cycles_kernel(int mode, size_t smem);
+cudaError_t occupancy_cycles(int mode, int threads, size_t smem, int* blocks_per_sm);
+cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int threads, size_t smem, cudaStream_t st,
+                          const DevProg& P, const DevState& S, const LaunchArgs& A);
+cudaError_t launch_commit(int grid, cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t_end,
+                          const uint64_t* t0_dev);
+cudaError_t launch_advance(cudaStream_t st, uint64_t* t0_dev, uint64_t n);
+cudaError_t launch_state_digest(cudaStream_t st, const DevProg& P, const DevState& S, uint32_t par,
+                                const uint64_t* mem_word_off, uint64_t mem_words, uint64_t* out, uint32_t n_inst);
+}  // namespace rtl
+
+using namespace rtl;
+
+namespace {
+
+thread_local std::string g_err;
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+int set_err(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return set_err(e_ == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA,      \
+                           std::string(#expr) + ": " + cudaGetErrorString(e_));               \
+    } while (0)
+
+uint64_t host_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+uint64_t mask_w(int w) { return w >= 64 ? ~0ULL : ((1ULL << w) - 1); }
+uint64_t reg_hash(uint64_t r) { return r * kGamma + 1ULL; }
+uint64_t mem_hash(uint64_t m, uint64_t a) { return reg_hash((1ULL << 40) + (m << 24) + a); }
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 152;
+    }
+    return n;
+}
+
+// A device allocation released with the owner.
+struct DBuf {
+    void* p = nullptr;
+    size_t n = 0;
+    ~DBuf() { reset(); }
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    int alloc(size_t bytes) {
+        reset();
+        n = bytes;
+        if (!bytes) return SIM_OK;
+        CUDA_TRY(cudaMalloc(&p, bytes));
+        return SIM_OK;
+    }
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+template <class T>
+int upload(DBuf& b, const std::vector<T>& v, cudaStream_t st) {
+    int rc = b.alloc(v.size() * sizeof(T));
+    if (rc) return rc;
+    if (!v.empty()) CUDA_TRY(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+    return SIM_OK;
+}
+
+}  // namespace
+
+struct sim_netlist {
+    sim_config cfg;
+    Netlist nl;
+    Partition part;
+    Lowered low;
+    RegLayout layout;
+    sim_netlist_info info{};
+    std::vector<uint32_t> mport_off, mport_id;
+    std::vector<uint64_t> mem_word_off;   // per-instance word offset of each memory (+ total)
+};
+
+struct sim_batch {
+    sim_netlist* nl = nullptr;
+    cudaStream_t stream = nullptr;
+    int mode = SIM_MODE_LANE_OP;
+    int kernel = SIM_KERNEL_PERSISTENT;
+    uint32_t n_inst = 0, I = 0;
+    uint64_t seed = 0, cycle = 0;
+    // program tables
+    DBuf s_ins, s_off, s_len, b_ins, b_off, b_len, mport_off, mport_id, mem_lg, mem_w, mem_base, in_w, reg_cls, reg_idx,
+        mem_word_off;
+    // state
+    DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, bar, err, t0_dev, scratch;
+    DevProg P{};
+    DevState S{};
+    std::vector<uint8_t> h_hold_flag;     // host mirror
+    std::vector<uint64_t> h_hold_val;
+    std::vector<int32_t> h_track;
+    std::vector<uint32_t> tracked;
+    // launch geometry
+    int threads = 256, warps = 8, grid = 0, max_grid = 0;
+    size_t smem = 0;
+    uint32_t slot_words = 0, n_tasks = 0;
+    uint64_t kernels_launched = 0;
+    int32_t skip_cta = -1;
+    uint64_t timeout_ns = 2000000000ULL;
+    // graph replay of per-cycle launches
+    cudaGraphExec_t graph = nullptr;
+    uint32_t graph_chunk = 0;
+    DevState graph_state{};               // state descriptor captured in the graph
+    bool own_stream = false;
+    ~sim_batch() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (own_stream && stream) cudaStreamDestroy(stream);
+    }
+    // copies ordered on the batch's stream, complete on return
+    int h2d(void* dst, const void* src, size_t n) {
+        if (!n) return SIM_OK;
+        CUDA_TRY(cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        return SIM_OK;
+    }
+    int d2h(void* dst, const void* src, size_t n) {
+        if (!n) return SIM_OK;
+        CUDA_TRY(cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, stream));
+        CUDA_TRY(cudaStreamSynchronize(stream));
+        return SIM_OK;
+    }
+};
+
+extern "C" {
+
+const char* sim_last_error(void) { return g_err.c_str(); }
+
+void sim_config_default(sim_config* cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof *cfg);
+    cfg->struct_size = sizeof(sim_config);
+    cfg->mode = SIM_MODE_AUTO;
+    cfg->kernel = SIM_KERNEL_PERSISTENT;
+    cfg->timeout_ms = 2000;
+    cfg->big_array_bytes = 128 * 1024;
+}
+
+int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_netlist** out) {
+    if (!text || !out) return set_err(SIM_ERR_BADARG, "null argument");
+    *out = nullptr;
+    try {
+        std::unique_ptr<sim_netlist> h(new sim_netlist());
+        sim_config_default(&h->cfg);
+        if (cfg) {
+            if (cfg->struct_size != sizeof(sim_config)) return set_err(SIM_ERR_BADARG, "sim_config.struct_size mismatch");
+            h->cfg = *cfg;
+        }
+        std::string err;
+        int rc = parse_netlist(static_cast<const char*>(text), len, h->nl, err);
+        if (rc) return set_err(rc, err);
+        PartitionConfig pc;
+        pc.big_array_bytes = h->cfg.big_array_bytes;
+        pc.stage3 = !h->cfg.disable_stage3;
+        pc.random_seed = h->cfg.seed_partition;
+        uint32_t target = h->cfg.target_processes;
+        if (!target) target = h->cfg.mode == SIM_MODE_LANE_INST ? 512 : uint32_t(sm_count()) * 8;
+        pc.target = target;
+        rc = partition(h->nl, pc, h->part, err);
+        if (rc) return set_err(rc, err);
+        rc = lower(h->nl, h->part, h->low, err);
+        if (rc) return set_err(rc, err);
+        h->layout = reg_layout(h->nl);
+        const Netlist& nl = h->nl;
+        h->mport_off.assign(1, 0);
+        for (auto& ports : nl.mem_ports) {
+            for (int32_t p : ports) h->mport_id.push_back(uint32_t(p));
+            h->mport_off.push_back(uint32_t(h->mport_id.size()));
+        }
+        h->mem_word_off.assign(1, 0);
+        for (uint8_t lg : nl.mem_lg) h->mem_word_off.push_back(h->mem_word_off.back() + (1ULL << lg));
+        sim_netlist_info& I = h->info;
+        I.n_inputs = uint32_t(nl.in_w.size());
+        I.n_regs = uint32_t(nl.reg_w.size());
+        I.n_mems = uint32_t(nl.mem_lg.size());
+        I.n_wports = uint32_t(nl.wports.size());
+        I.n_nodes = nl.nodes.size();
+        I.n_ops = nl.n_ops;
+        I.n_fibers = uint32_t(h->part.fibers.size());
+        I.n_processes = uint32_t(h->part.procs.size());
+        I.fiber_cost_sum = h->part.fiber_cost_sum;
+        I.fiber_cost_max = h->part.fiber_cost_max;
+        I.process_cost_sum = h->part.proc_cost_sum;
+        I.process_cost_max = h->part.proc_cost_max;
+        I.max_bundles = h->low.max_bundles;
+        I.max_slots = std::max(h->low.max_s_slots, h->low.max_b_slots);
+        I.instr_count = h->low.b_ins.size();
+        I.cut_words = h->part.cut_words;
+        *out = h.release();
+        return SIM_OK;
+    } catch (const std::bad_alloc&) {
+        return set_err(SIM_ERR_OOM, "host allocation failed");
+    } catch (const std::exception& e) {
+        return set_err(SIM_ERR_PARSE, e.what());
+    }
+}
+
+int sim_netlist_get_info(const sim_netlist* nl, sim_netlist_info* out) {
+    if (!nl || !out) return set_err(SIM_ERR_BADARG, "null argument");
+    *out = nl->info;
+    return SIM_OK;
+}
+
+void sim_netlist_destroy(sim_netlist* nl) { delete nl; }
+
+int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* bytes) {
+    if (!nl || !bytes) return set_err(SIM_ERR_BADARG, "null argument");
+    const Lowered& L = nl->low;
+    const Partition& P = nl->part;
+    std::vector<int32_t> i32;
+    std::vector<uint64_t> u64;
+    const void* src = nullptr;
+    size_t n = 0;
+    auto pick = [&](const auto& v) {
+        src = v.data();
+        n = v.size() * sizeof(v[0]);
+    };
+    switch (which) {
+    case 0: pick(L.s_ins); break;
+    case 1: pick(L.s_off); break;
+    case 2: pick(L.s_len); break;
+    case 3: pick(L.b_ins); break;
+    case 4: pick(L.b_off); break;
+    case 5: pick(L.b_len); break;
+    case 6:
+        i32.assign(P.fibers.size(), -1);
+        for (size_t p = 0; p < P.procs.size(); p++)
+            for (int32_t f : P.procs[p]) i32[f] = int32_t(p);
+        pick(i32);
+        break;
+    case 7:
+        for (auto& f : P.fibers) i32.push_back(f.reg >= 0 ? f.reg : -1 - f.mem);
+        pick(i32);
+        break;
+    case 8:
+        for (auto& f : P.fibers) u64.push_back(f.cost);
+        pick(u64);
+        break;
+    case 9: pick(P.proc_cost); break;
+    case 10: pick(nl->layout.cls); break;
+    case 11: pick(nl->layout.idx); break;
+    case 12: pick(L.s_slots); break;
+    case 13: pick(L.b_slots); break;
+    default: return set_err(SIM_ERR_BADARG, "unknown table");
+    }
+    if (out) memcpy(out, src, std::min(n, *bytes));
+    *bytes = n;
+    return SIM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Choose warps per CTA and grid for a batch (both lane mappings).
+int plan_launch(sim_batch* b) {
+    const Lowered& L = b->nl->low;
+    const int sms = sm_count();
+    const size_t smem_cap = 220 * 1024;
+    if (b->mode == SIM_MODE_LANE_INST) {
+        b->slot_words = L.max_b_slots * 32;
+        b->n_tasks = uint32_t(b->nl->part.procs.size()) * (b->I / 32);
+    } else {
+        b->slot_words = L.max_s_slots;
+        b->n_tasks = uint32_t(b->nl->part.procs.size()) * b->I;
+    }
+    size_t per_warp = size_t(b->slot_words) * 8;
+    if (per_warp > smem_cap)
+        return set_err(SIM_ERR_CAPACITY, "a process needs " + std::to_string(per_warp) +
+                                             " bytes of value slots per warp (limit " + std::to_string(smem_cap) + ")");
+    int warps = b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8;
+    while (warps > 1 && size_t(warps) * per_warp > smem_cap) warps /= 2;
+    b->warps = warps;
+    b->threads = warps * 32;
+    b->smem = size_t(warps) * per_warp;
+    CUDA_TRY(prepare_cycles_kernel(b->mode, b->smem));
+    int occ = 0;
+    CUDA_TRY(occupancy_cycles(b->mode, b->threads, b->smem, &occ));
+    if (occ < 1) return set_err(SIM_ERR_CAPACITY, "kernel does not fit on an SM");
+    b->max_grid = occ * sms;
+    int need = int((b->n_tasks + warps - 1) / warps);
+    b->grid = std::max(1, std::min(need, b->max_grid));
+    return SIM_OK;
+}
+
+int upload_program(sim_batch* b) {
+    sim_netlist* h = b->nl;
+    const Netlist& nl = h->nl;
+    const Lowered& L = h->low;
+    cudaStream_t st = b->stream;
+    int rc;
+    std::vector<uint64_t> mem_base(nl.mem_lg.size());
+    for (size_t m = 0; m < nl.mem_lg.size(); m++) mem_base[m] = h->mem_word_off[m] * b->I;
+    if ((rc = upload(b->s_ins, L.s_ins, st)) || (rc = upload(b->s_off, L.s_off, st)) || (rc = upload(b->s_len, L.s_len, st)) ||
+        (rc = upload(b->b_ins, L.b_ins, st)) || (rc = upload(b->b_off, L.b_off, st)) || (rc = upload(b->b_len, L.b_len, st)) ||
+        (rc = upload(b->mport_off, h->mport_off, st)) || (rc = upload(b->mport_id, h->mport_id, st)) ||
+        (rc = upload(b->mem_lg, nl.mem_lg, st)) || (rc = upload(b->mem_w, nl.mem_w, st)) ||
+        (rc = upload(b->mem_base, mem_base, st)) || (rc = upload(b->in_w, nl.in_w, st)) ||
+        (rc = upload(b->reg_cls, h->layout.cls, st)) || (rc = upload(b->reg_idx, h->layout.idx, st)) ||
+        (rc = upload(b->mem_word_off, h->mem_word_off, st)))
+        return rc;
+    DevProg& P = b->P;
+    P.s_ins = b->s_ins.as<DIns>();
+    P.s_off = b->s_off.as<uint32_t>();
+    P.s_len = b->s_len.as<uint32_t>();
+    P.b_ins = b->b_ins.as<DIns>();
+    P.b_off = b->b_off.as<uint32_t>();
+    P.b_len = b->b_len.as<uint32_t>();
+    P.mport_off = b->mport_off.as<uint32_t>();
+    P.mport_id = b->mport_id.as<uint32_t>();
+    P.mem_lg = b->mem_lg.as<uint8_t>();
+    P.mem_w = b->mem_w.as<uint8_t>();
+    P.mem_base = b->mem_base.as<uint64_t>();
+    P.in_w = b->in_w.as<uint8_t>();
+    P.reg_cls = b->reg_cls.as<uint8_t>();
+    P.reg_idx = b->reg_idx.as<uint32_t>();
+    P.n_proc = uint32_t(h->part.procs.size());
+    P.n_in = uint32_t(nl.in_w.size());
+    P.n_reg = uint32_t(nl.reg_w.size());
+    P.n_mem = uint32_t(nl.mem_lg.size());
+    P.n_wport = uint32_t(nl.wports.size());
+    return SIM_OK;
+}
+
+// Initial state: register init values, memory images, keys, digests.
+int init_state(sim_batch* b) {
+    sim_netlist* h = b->nl;
+    const Netlist& nl = h->nl;
+    const RegLayout& L = h->layout;
+    cudaStream_t st = b->stream;
+    const uint64_t I = b->I;
+    DevState& S = b->S;
+    S.I = b->I;
+    S.pack = b->mode == SIM_MODE_LANE_INST ? 32 : 1;
+    S.bit_stride = uint32_t((I + S.pack - 1) / S.pack);
+    int rc;
+    for (int k = 0; k < 2; k++) {
+        if ((rc = b->bits[k].alloc(size_t(L.count[RC_BIT]) * S.bit_stride * 4)) ||
+            (rc = b->w32[k].alloc(size_t(L.count[RC_W32]) * I * 4)) || (rc = b->w64[k].alloc(size_t(L.count[RC_W64]) * I * 8)) ||
+            (rc = b->rec[k].alloc(nl.wports.size() * I * 16)))
+            return rc;
+        S.bits[k] = b->bits[k].as<uint32_t>();
+        S.w32[k] = b->w32[k].as<uint32_t>();
+        S.w64[k] = b->w64[k].as<uint64_t>();
+        S.rec[k] = b->rec[k].as<uint64_t>();
+        if (b->rec[k].n) CUDA_TRY(cudaMemsetAsync(b->rec[k].p, 0, b->rec[k].n, st));
+    }
+    // register planes of buffer 0 from init values (host-built, one plane at a time)
+    {
+        std::vector<uint32_t> bitw(size_t(L.count[RC_BIT]) * S.bit_stride);
+        std::vector<uint32_t> w32(size_t(L.count[RC_W32]) * I);
+        std::vector<uint64_t> w64(size_t(L.count[RC_W64]) * I);
+        for (size_t r = 0; r < nl.reg_w.size(); r++) {
+            uint64_t v = nl.reg_init[r];
+            uint32_t ix = L.idx[r];
+            if (L.cls[r] == RC_W64) std::fill(w64.begin() + size_t(ix) * I, w64.begin() + size_t(ix + 1) * I, v);
+            else if (L.cls[r] == RC_W32) std::fill(w32.begin() + size_t(ix) * I, w32.begin() + size_t(ix + 1) * I, uint32_t(v));
+            else {
+                uint32_t word = (v & 1) ? (S.pack == 32 ? 0xffffffffu : 1u) : 0u;
+                std::fill(bitw.begin() + size_t(ix) * S.bit_stride, bitw.begin() + size_t(ix + 1) * S.bit_stride, word);
+            }
+        }
+        if (!bitw.empty()) CUDA_TRY(cudaMemcpyAsync(S.bits[0], bitw.data(), bitw.size() * 4, cudaMemcpyHostToDevice, st));
+        if (!w32.empty()) CUDA_TRY(cudaMemcpyAsync(S.w32[0], w32.data(), w32.size() * 4, cudaMemcpyHostToDevice, st));
+        if (!w64.empty()) CUDA_TRY(cudaMemcpyAsync(S.w64[0], w64.data(), w64.size() * 8, cudaMemcpyHostToDevice, st));
+        CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // memories
+    const uint64_t words = h->mem_word_off.back();
+    if ((rc = b->mem.alloc(size_t(words) * I * 8))) return rc;
+    S.mem = b->mem.as<uint64_t>();
+    if (b->mem.n) {
+        CUDA_TRY(cudaMemsetAsync(S.mem, 0, b->mem.n, st));
+        std::vector<uint64_t> row(I);
+        for (size_t m = 0; m < nl.mem_lg.size(); m++)
+            for (auto& [a, v] : nl.mem_init[m]) {
+                std::fill(row.begin(), row.end(), v);
+                CUDA_TRY(cudaMemcpyAsync(S.mem + (h->mem_word_off[m] + a) * I, row.data(), I * 8, cudaMemcpyHostToDevice, st));
+                CUDA_TRY(cudaStreamSynchronize(st));
+            }
+    }
+    // stimulus keys: output inst+1 of the SplitMix64 stream seeded with `seed`
+    {
+        std::vector<uint64_t> keys(I);
+        for (uint64_t i = 0; i < I; i++) keys[i] = host_mix64(b->seed + (i + 1) * kGamma);
+        if ((rc = upload(b->key, keys, st))) return rc;
+        S.key = b->key.as<uint64_t>();
+    }
+    b->h_hold_flag.assign(nl.in_w.size() * I, 0);
+    b->h_hold_val.assign(nl.in_w.size() * I, 0);
+    if ((rc = upload(b->hold_flag, b->h_hold_flag, st)) || (rc = upload(b->hold_val, b->h_hold_val, st))) return rc;
+    S.hold_flag = b->hold_flag.as<uint8_t>();
+    S.hold_val = b->hold_val.as<uint64_t>();
+    S.any_hold = 0;
+    // memory digest part (same initial image in every instance)
+    {
+        std::vector<uint64_t> md(nl.mem_lg.size() * I);
+        for (size_t m = 0; m < nl.mem_lg.size(); m++) {
+            std::vector<uint64_t> img(1ULL << nl.mem_lg[m], 0);
+            for (auto& [a, v] : nl.mem_init[m]) img[a] = v;
+            uint64_t d = 0;
+            for (uint64_t a = 0; a < img.size(); a++) d += host_mix64(mem_hash(m, a) ^ img[a]);
+            std::fill(md.begin() + m * I, md.begin() + (m + 1) * I, d);
+        }
+        if ((rc = upload(b->mem_dig, md, st))) return rc;
+        S.mem_dig = b->mem_dig.as<uint64_t>();
+    }
+    if ((rc = b->bar.alloc(16)) || (rc = b->err.alloc(16)) || (rc = b->t0_dev.alloc(8))) return rc;
+    S.bar = b->bar.as<uint32_t>();
+    S.err = b->err.as<int32_t>();
+    CUDA_TRY(cudaMemsetAsync(b->bar.p, 0, 16, st));
+    CUDA_TRY(cudaMemsetAsync(b->err.p, 0, 16, st));
+    CUDA_TRY(cudaMemsetAsync(b->t0_dev.p, 0, 8, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    return SIM_OK;
+}
+
+// Digest of the initial state (identical for every instance).
+uint64_t initial_digest(const sim_netlist* h) {
+    const Netlist& nl = h->nl;
+    uint64_t d = 0;
+    for (size_t r = 0; r < nl.reg_w.size(); r++) d += host_mix64(reg_hash(r) ^ nl.reg_init[r]);
+    for (size_t m = 0; m < nl.mem_lg.size(); m++) {
+        std::vector<uint64_t> img(1ULL << nl.mem_lg[m], 0);
+        for (auto& [a, v] : nl.mem_init[m]) img[a] = v;
+        for (uint64_t a = 0; a < img.size(); a++) d += host_mix64(mem_hash(m, a) ^ img[a]);
+    }
+    return d;
+}
+
+int setup_tracking(sim_batch* b, const std::vector<uint32_t>& insts) {
+    sim_netlist* h = b->nl;
+    const uint32_t cap = h->cfg.digest_capacity;
+    DevState& S = b->S;
+    b->tracked = insts;
+    b->h_track.assign(b->I, -1);
+    for (size_t k = 0; k < insts.size(); k++) b->h_track[insts[k]] = int32_t(k);
+    int rc = upload(b->track, b->h_track, b->stream);
+    if (rc) return rc;
+    S.track = b->track.as<int32_t>();
+    S.ring_cap = cap;
+    S.n_tracked = uint32_t(insts.size());
+    if (cap && !insts.empty()) {
+        std::vector<uint64_t> ring(size_t(cap) * insts.size(), 0);
+        uint64_t d0 = initial_digest(h);
+        for (size_t k = 0; k < insts.size(); k++) ring[k] = d0;   // state 0 in slot 0
+        if ((rc = upload(b->ring, ring, b->stream))) return rc;
+        S.ring = b->ring.as<uint64_t>();
+    } else {
+        S.ring_cap = 0;
+        S.ring = nullptr;
+    }
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return SIM_OK;
+}
+
+int check_err(sim_batch* b) {
+    int32_t e = 0;
+    CUDA_TRY(cudaMemcpyAsync(&e, b->err.p, 4, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    if (e) {
+        CUDA_TRY(cudaMemsetAsync(b->err.p, 0, 4, b->stream));
+        return set_err(e, e == SIM_ERR_TIMEOUT ? "grid barrier wait timed out" : "device error");
+    }
+    return SIM_OK;
+}
+
+LaunchArgs base_args(sim_batch* b) {
+    LaunchArgs A{};
+    A.t0_dev = nullptr;
+    A.skip_cta = -1;
+    A.timeout_ns = b->timeout_ns;
+    A.warps_per_cta = uint32_t(b->warps);
+    A.slot_words = b->slot_words;
+    A.n_tasks = b->n_tasks;
+    A.group = b->mode == SIM_MODE_LANE_INST ? 32 : 1;
+    return A;
+}
+
+// Zero the ring slots of cycles t0+1 .. t0+n before they are accumulated.
+int clear_ring(sim_batch* b, uint64_t t0, uint64_t n) {
+    DevState& S = b->S;
+    if (!S.ring_cap) return SIM_OK;
+    const size_t row = size_t(S.n_tracked) * 8;
+    for (uint64_t t = t0 + 1; t <= t0 + n; t++) {
+        uint64_t s = t % S.ring_cap;
+        uint64_t run = std::min<uint64_t>(t0 + n - t + 1, S.ring_cap - s);
+        CUDA_TRY(cudaMemsetAsync(S.ring + s * S.n_tracked, 0, row * run, b->stream));
+        t += run - 1;
+    }
+    return SIM_OK;
+}
+
+int step_persistent(sim_batch* b, uint64_t n) {
+    LaunchArgs A = base_args(b);
+    A.t0 = b->cycle;
+    A.n = uint32_t(n);
+    A.pending_first = 0;
+    A.grid_sync = 1;
+    A.skip_cta = b->skip_cta;
+    b->skip_cta = -1;
+    CUDA_TRY(cudaMemsetAsync(b->bar.p, 0, 8, b->stream));
+    CUDA_TRY(launch_cycles(b->mode, b->S.ring_cap > 0, true, b->grid, b->threads, b->smem, b->stream, b->P, b->S, A));
+    b->kernels_launched++;
+    return SIM_OK;
+}
+
+int step_per_cycle(sim_batch* b, uint64_t n) {
+    LaunchArgs A = base_args(b);
+    A.n = 1;
+    A.grid_sync = 0;
+    int grid = std::max(1, int((b->n_tasks + b->warps - 1) / b->warps));
+    for (uint64_t k = 0; k < n; k++) {
+        A.t0 = b->cycle + k;
+        A.pending_first = k > 0;
+        CUDA_TRY(launch_cycles(b->mode, b->S.ring_cap > 0, false, grid, b->threads, b->smem, b->stream, b->P, b->S, A));
+    }
+    CUDA_TRY(launch_commit(std::max(1, b->grid), b->stream, b->P, b->S, b->cycle + n, nullptr));
+    b->kernels_launched += n + 1;
+    return SIM_OK;
+}
+
+// Per-cycle launches replayed from a captured CUDA graph: one graph holds
+// `chunk` cycle launches, the final commit and the advance of the device
+// cycle base, so it can be replayed for any starting cycle.
+int step_graph(sim_batch* b, uint64_t n) {
+    const uint32_t chunk = 64;
+    if (!b->graph || b->graph_chunk != chunk || memcmp(&b->graph_state, &b->S, sizeof(DevState)) != 0) {
+        b->graph_state = b->S;
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        cudaGraph_t g;
+        CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        LaunchArgs A = base_args(b);
+        A.t0_dev = b->t0_dev.as<uint64_t>();
+        A.n = 1;
+        A.grid_sync = 0;
+        int grid = std::max(1, int((b->n_tasks + b->warps - 1) / b->warps));
+        cudaError_t e = cudaSuccess;
+        for (uint32_t k = 0; k < chunk && e == cudaSuccess; k++) {
+            A.t0 = k;
+            A.pending_first = k > 0;
+            e = launch_cycles(b->mode, b->S.ring_cap > 0, false, grid, b->threads, b->smem, b->stream, b->P, b->S, A);
+        }
+        if (e == cudaSuccess) e = launch_commit(std::max(1, b->grid), b->stream, b->P, b->S, chunk, A.t0_dev);
+        if (e == cudaSuccess) e = launch_advance(b->stream, b->t0_dev.as<uint64_t>(), chunk);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return set_err(SIM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_TRY(e);
+        b->graph_chunk = chunk;
+    }
+    uint64_t done = 0;
+    CUDA_TRY(cudaMemcpyAsync(b->t0_dev.p, &b->cycle, 8, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    while (n - done >= chunk) {
+        CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
+        b->kernels_launched += chunk + 2;
+        done += chunk;
+    }
+    if (done < n) {
+        uint64_t save = b->cycle;
+        b->cycle += done;
+        int rc = step_per_cycle(b, n - done);
+        b->cycle = save;
+        if (rc) return rc;
+    }
+    return SIM_OK;
+}
+
+sim_batch* B(void* p) { return static_cast<sim_batch*>(p); }
+
+int check_inst(sim_batch* b, uint32_t inst) {
+    if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    if (inst >= b->n_inst) return set_err(SIM_ERR_BADARG, "instance out of range");
+    return SIM_OK;
+}
+
+// Address of register r of `inst` in buffer par (device pointer, element size, bit).
+void reg_addr(sim_batch* b, uint32_t par, uint32_t r, uint32_t inst, void** p, int* bytes, int* bit) {
+    const RegLayout& L = b->nl->layout;
+    uint64_t ix = L.idx[r];
+    const DevState& S = b->S;
+    *bit = -1;
+    if (L.cls[r] == RC_W64) { *p = S.w64[par] + ix * S.I + inst; *bytes = 8; }
+    else if (L.cls[r] == RC_W32) { *p = S.w32[par] + ix * S.I + inst; *bytes = 4; }
+    else { *p = S.bits[par] + ix * S.bit_stride + inst / S.pack; *bytes = 4; *bit = int(inst % S.pack); }
+}
+
+}  // namespace
+
+extern "C" {
+
+int sim_create_instances(sim_netlist* nl, uint32_t n_inst, uint64_t seed, void* cuda_stream, sim_batch** out) {
+    if (!nl || !out || n_inst == 0) return set_err(SIM_ERR_BADARG, "bad argument");
+    *out = nullptr;
+    try {
+        std::unique_ptr<sim_batch> b(new sim_batch());
+        b->nl = nl;
+        b->stream = static_cast<cudaStream_t>(cuda_stream);
+        if (!b->stream) {     // a private stream (graph capture needs a non-legacy stream)
+            CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
+            b->own_stream = true;
+        }
+        b->n_inst = n_inst;
+        b->seed = seed;
+        b->mode = nl->cfg.mode == SIM_MODE_AUTO ? (n_inst >= 32 ? SIM_MODE_LANE_INST : SIM_MODE_LANE_OP) : nl->cfg.mode;
+        b->kernel = nl->cfg.kernel;
+        b->I = b->mode == SIM_MODE_LANE_INST ? (n_inst + 31) / 32 * 32 : n_inst;
+        b->timeout_ns = uint64_t(nl->cfg.timeout_ms ? nl->cfg.timeout_ms : 2000) * 1000000ULL;
+        int rc;
+        if ((rc = upload_program(b.get())) || (rc = init_state(b.get())) || (rc = plan_launch(b.get()))) return rc;
+        if ((rc = setup_tracking(b.get(), {0}))) return rc;
+        *out = b.release();
+        return SIM_OK;
+    } catch (const std::bad_alloc&) {
+        return set_err(SIM_ERR_OOM, "host allocation failed");
+    }
+}
+
+void sim_batch_destroy(sim_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    delete b;
+}
+
+int sim_track_digests(sim_batch* b, const uint32_t* insts, uint32_t n) {
+    if (!b || (n && !insts)) return set_err(SIM_ERR_BADARG, "bad argument");
+    if (b->cycle != 0) return set_err(SIM_ERR_STATE, "digest tracking must be set before the first step");
+    std::vector<uint32_t> v(insts, insts + n);
+    for (uint32_t i : v)
+        if (i >= b->n_inst) return set_err(SIM_ERR_BADARG, "tracked instance out of range");
+    return setup_tracking(b, v);
+}
+
+int sim_step(sim_batch* b, uint64_t n_cycles) {
+    if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    if (n_cycles == 0) return SIM_OK;
+    const uint32_t cap = b->S.ring_cap;
+    uint64_t left = n_cycles;
+    while (left) {
+        // with digests on, a launch may not wrap the ring
+        uint64_t n = cap ? std::min<uint64_t>(left, cap - 1) : std::min<uint64_t>(left, 1u << 30);
+        int rc = clear_ring(b, b->cycle, n);
+        if (rc) return rc;
+        if (b->kernel == SIM_KERNEL_PER_CYCLE) rc = step_per_cycle(b, n);
+        else if (b->kernel == SIM_KERNEL_PER_CYCLE_GRAPH) rc = step_graph(b, n);
+        else rc = step_persistent(b, n);
+        if (rc) return rc;
+        b->cycle += n;
+        left -= n;
+    }
+    return SIM_OK;
+}
+
+int sim_sync(sim_batch* b) {
+    if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return check_err(b);
+}
+
+int sim_cycle(sim_batch* b, uint64_t* out) {
+    if (!b || !out) return set_err(SIM_ERR_BADARG, "null argument");
+    *out = b->cycle;
+    return SIM_OK;
+}
+
+int sim_poke(sim_batch* b, uint32_t inst, int32_t kind, uint32_t index, uint64_t value) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    const Netlist& nl = b->nl->nl;
+    rc = sim_sync(b);
+    if (rc) return rc;
+    if (kind == SIM_SIG_INPUT) {
+        if (index >= nl.in_w.size()) return set_err(SIM_ERR_BADARG, "input out of range");
+        size_t j = size_t(index) * b->I + inst;
+        b->h_hold_flag[j] = 1;
+        b->h_hold_val[j] = value & mask_w(nl.in_w[index]);
+        CUDA_TRY(cudaMemcpyAsync(b->hold_flag.as<uint8_t>() + j, &b->h_hold_flag[j], 1, cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(b->hold_val.as<uint64_t>() + j, &b->h_hold_val[j], 8, cudaMemcpyHostToDevice, b->stream));
+        b->S.any_hold = 1;
+        CUDA_TRY(cudaStreamSynchronize(b->stream));
+        return SIM_OK;
+    }
+    if (kind != SIM_SIG_REG) return set_err(SIM_ERR_BADARG, "bad signal kind");
+    if (index >= nl.reg_w.size()) return set_err(SIM_ERR_BADARG, "register out of range");
+    value &= mask_w(nl.reg_w[index]);
+    void* p;
+    int bytes, bit;
+    reg_addr(b, uint32_t(b->cycle & 1), index, inst, &p, &bytes, &bit);
+    if (bit < 0) {
+        if ((rc = b->h2d(p, &value, bytes))) return rc;
+    } else {
+        uint32_t word;
+        if ((rc = b->d2h(&word, p, 4))) return rc;
+        word = (word & ~(1u << bit)) | (uint32_t(value & 1) << bit);
+        if ((rc = b->h2d(p, &word, 4))) return rc;
+    }
+    return SIM_OK;
+}
+
+int sim_unpoke(sim_batch* b, uint32_t inst, uint32_t input) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    if (input >= b->nl->nl.in_w.size()) return set_err(SIM_ERR_BADARG, "input out of range");
+    rc = sim_sync(b);
+    if (rc) return rc;
+    size_t j = size_t(input) * b->I + inst;
+    b->h_hold_flag[j] = 0;
+    if ((rc = b->h2d(b->hold_flag.as<uint8_t>() + j, &b->h_hold_flag[j], 1))) return rc;
+    b->S.any_hold = std::any_of(b->h_hold_flag.begin(), b->h_hold_flag.end(), [](uint8_t f) { return f != 0; });
+    return SIM_OK;
+}
+
+int sim_poke_mem(sim_batch* b, uint32_t inst, uint32_t mem, uint64_t addr, uint64_t value) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    const Netlist& nl = b->nl->nl;
+    if (mem >= nl.mem_lg.size() || addr >= (1ULL << nl.mem_lg[mem])) return set_err(SIM_ERR_BADARG, "memory address out of range");
+    rc = sim_sync(b);
+    if (rc) return rc;
+    value &= mask_w(nl.mem_w[mem]);
+    uint64_t* cell = b->S.mem + (b->nl->mem_word_off[mem] + addr) * b->I + inst;
+    uint64_t old, md;
+    if ((rc = b->d2h(&old, cell, 8))) return rc;
+    if ((rc = b->h2d(cell, &value, 8))) return rc;
+    uint64_t* mdp = b->S.mem_dig + size_t(mem) * b->I + inst;
+    if ((rc = b->d2h(&md, mdp, 8))) return rc;
+    md += host_mix64(mem_hash(mem, addr) ^ value) - host_mix64(mem_hash(mem, addr) ^ old);
+    if ((rc = b->h2d(mdp, &md, 8))) return rc;
+    return SIM_OK;
+}
+
+int sim_peek(sim_batch* b, uint32_t inst, int32_t kind, uint32_t index, uint64_t* out) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    if (!out) return set_err(SIM_ERR_BADARG, "null output");
+    const Netlist& nl = b->nl->nl;
+    rc = sim_sync(b);
+    if (rc) return rc;
+    if (kind == SIM_SIG_INPUT) {
+        if (index >= nl.in_w.size()) return set_err(SIM_ERR_BADARG, "input out of range");
+        size_t j = size_t(index) * b->I + inst;
+        if (b->h_hold_flag[j]) *out = b->h_hold_val[j];
+        else {
+            uint64_t key = host_mix64(b->seed + (uint64_t(inst) + 1) * kGamma);
+            *out = host_mix64(key + (b->cycle * nl.in_w.size() + index + 1) * kGamma) & mask_w(nl.in_w[index]);
+        }
+        return SIM_OK;
+    }
+    if (kind != SIM_SIG_REG) return set_err(SIM_ERR_BADARG, "bad signal kind");
+    if (index >= nl.reg_w.size()) return set_err(SIM_ERR_BADARG, "register out of range");
+    void* p;
+    int bytes, bit;
+    reg_addr(b, uint32_t(b->cycle & 1), index, inst, &p, &bytes, &bit);
+    uint64_t v = 0;
+    if ((rc = b->d2h(&v, p, bytes))) return rc;
+    if (bit >= 0) v = (v >> bit) & 1;
+    *out = v;
+    return SIM_OK;
+}
+
+int sim_peek_mem(sim_batch* b, uint32_t inst, uint32_t mem, uint64_t addr, uint64_t* out) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    const Netlist& nl = b->nl->nl;
+    if (!out || mem >= nl.mem_lg.size() || addr >= (1ULL << nl.mem_lg[mem])) return set_err(SIM_ERR_BADARG, "bad argument");
+    rc = sim_sync(b);
+    if (rc) return rc;
+    if ((rc = b->d2h(out, b->S.mem + (b->nl->mem_word_off[mem] + addr) * b->I + inst, 8))) return rc;
+    return SIM_OK;
+}
+
+int sim_peek_regs(sim_batch* b, uint32_t inst, uint64_t* out) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    if (!out) return set_err(SIM_ERR_BADARG, "null output");
+    rc = sim_sync(b);
+    if (rc) return rc;
+    const RegLayout& L = b->nl->layout;
+    const DevState& S = b->S;
+    const uint32_t par = uint32_t(b->cycle & 1);
+    std::vector<uint64_t> v64(L.count[RC_W64]);
+    std::vector<uint32_t> v32(L.count[RC_W32]), v1(L.count[RC_BIT]);
+    if (!v64.empty())
+        CUDA_TRY(cudaMemcpy2DAsync(v64.data(), 8, S.w64[par] + inst, size_t(S.I) * 8, 8, v64.size(),
+                                   cudaMemcpyDeviceToHost, b->stream));
+    if (!v32.empty())
+        CUDA_TRY(cudaMemcpy2DAsync(v32.data(), 4, S.w32[par] + inst, size_t(S.I) * 4, 4, v32.size(),
+                                   cudaMemcpyDeviceToHost, b->stream));
+    if (!v1.empty())
+        CUDA_TRY(cudaMemcpy2DAsync(v1.data(), 4, S.bits[par] + inst / S.pack, size_t(S.bit_stride) * 4, 4, v1.size(),
+                                   cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    for (size_t r = 0; r < L.cls.size(); r++) {
+        uint32_t ix = L.idx[r];
+        if (L.cls[r] == RC_W64) out[r] = v64[ix];
+        else if (L.cls[r] == RC_W32) out[r] = v32[ix];
+        else out[r] = (v1[ix] >> (inst % S.pack)) & 1;
+    }
+    return SIM_OK;
+}
+
+int sim_state_digests(sim_batch* b, uint64_t* out) {
+    if (!b || !out) return set_err(SIM_ERR_BADARG, "null argument");
+    int rc = sim_sync(b);
+    if (rc) return rc;
+    if (b->scratch.n < size_t(b->I) * 8)
+        if ((rc = b->scratch.alloc(size_t(b->I) * 8))) return rc;
+    uint64_t* d = b->scratch.as<uint64_t>();
+    CUDA_TRY(cudaMemsetAsync(d, 0, size_t(b->I) * 8, b->stream));
+    CUDA_TRY(launch_state_digest(b->stream, b->P, b->S, uint32_t(b->cycle & 1), b->mem_word_off.as<uint64_t>(),
+                                 b->nl->mem_word_off.back(), d, b->I));
+    b->kernels_launched++;
+    CUDA_TRY(cudaMemcpyAsync(out, d, size_t(b->n_inst) * 8, cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return SIM_OK;
+}
+
+int sim_digests(sim_batch* b, uint32_t inst, uint64_t first_cycle, uint64_t n, uint64_t* out) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    if (!out && n) return set_err(SIM_ERR_BADARG, "null output");
+    const DevState& S = b->S;
+    if (!S.ring_cap) return set_err(SIM_ERR_STATE, "digests are off (sim_config.digest_capacity = 0)");
+    int col = b->h_track[inst];
+    if (col < 0) return set_err(SIM_ERR_STATE, "instance is not tracked");
+    if (n == 0) return SIM_OK;
+    if (first_cycle + n - 1 > b->cycle || first_cycle + S.ring_cap <= b->cycle)
+        return set_err(SIM_ERR_BADARG, "requested cycles are not in the digest ring");
+    rc = sim_sync(b);
+    if (rc) return rc;
+    std::vector<uint64_t> ring(size_t(S.ring_cap) * S.n_tracked);
+    if ((rc = b->d2h(ring.data(), S.ring, ring.size() * 8))) return rc;
+    for (uint64_t k = 0; k < n; k++) out[k] = ring[((first_cycle + k) % S.ring_cap) * S.n_tracked + col];
+    return SIM_OK;
+}
+
+int sim_step_host(sim_batch* b, uint64_t n_cycles, const uint64_t* held_inputs, uint64_t* out_digests) {
+    if (!b || !out_digests) return set_err(SIM_ERR_BADARG, "null argument");
+    const size_t n_in = b->nl->nl.in_w.size();
+    if (held_inputs && n_in) {
+        // host layout [inst][input] -> device [input][inst]
+        for (size_t k = 0; k < n_in; k++)
+            for (uint32_t i = 0; i < b->n_inst; i++) {
+                b->h_hold_val[k * b->I + i] = held_inputs[size_t(i) * n_in + k] & mask_w(b->nl->nl.in_w[k]);
+                b->h_hold_flag[k * b->I + i] = 1;
+            }
+        CUDA_TRY(cudaMemcpyAsync(b->hold_val.p, b->h_hold_val.data(), b->h_hold_val.size() * 8, cudaMemcpyHostToDevice, b->stream));
+        CUDA_TRY(cudaMemcpyAsync(b->hold_flag.p, b->h_hold_flag.data(), b->h_hold_flag.size(), cudaMemcpyHostToDevice, b->stream));
+        b->S.any_hold = 1;
+    }
+    int rc = sim_step(b, n_cycles);
+    if (rc) return rc;
+    return sim_state_digests(b, out_digests);
+}
+
+// ---- checkpoints -----------------------------------------------------------
+namespace {
+struct BlobHeader {
+    uint64_t magic, version, n_reg, n_mem_words, I, mode, cycle, n_in;
+};
+constexpr uint64_t kMagic = 0x314B505453525447ULL;
+}  // namespace
+
+int sim_save(sim_batch* b, void** blob, size_t* len) {
+    if (!b || !blob || !len) return set_err(SIM_ERR_BADARG, "null argument");
+    int rc = sim_sync(b);
+    if (rc) return rc;
+    const RegLayout& L = b->nl->layout;
+    const DevState& S = b->S;
+    const uint32_t par = uint32_t(b->cycle & 1);
+    size_t nb = size_t(L.count[RC_BIT]) * S.bit_stride * 4, n32 = size_t(L.count[RC_W32]) * S.I * 4,
+           n64 = size_t(L.count[RC_W64]) * S.I * 8, nm = b->mem.n, nmd = b->mem_dig.n, nh = b->h_hold_val.size();
+    size_t total = sizeof(BlobHeader) + nb + n32 + n64 + nm + nmd + nh * 9;
+    char* p = static_cast<char*>(malloc(total));
+    if (!p) return set_err(SIM_ERR_OOM, "host allocation failed");
+    BlobHeader h{kMagic, 1, b->nl->nl.reg_w.size(), b->nl->mem_word_off.back(), S.I, uint64_t(b->mode), b->cycle, b->nl->nl.in_w.size()};
+    memcpy(p, &h, sizeof h);
+    char* q = p + sizeof h;
+    auto d2h = [&](const void* src, size_t n) {
+        if (n && b->d2h(q, src, n) != SIM_OK) return false;
+        q += n;
+        return true;
+    };
+    if (!d2h(S.bits[par], nb) || !d2h(S.w32[par], n32) || !d2h(S.w64[par], n64) || !d2h(S.mem, nm) || !d2h(S.mem_dig, nmd)) {
+        free(p);
+        return set_err(SIM_ERR_CUDA, "checkpoint copy failed");
+    }
+    if (nh) {
+        memcpy(q, b->h_hold_val.data(), nh * 8);
+        q += nh * 8;
+        memcpy(q, b->h_hold_flag.data(), nh);
+    }
+    *blob = p;
+    *len = total;
+    return SIM_OK;
+}
+
+int sim_restore(sim_batch* b, const void* blob, size_t len) {
+    if (!b || !blob) return set_err(SIM_ERR_BADARG, "null argument");
+    int rc = sim_sync(b);
+    if (rc) return rc;
+    BlobHeader h;
+    if (len < sizeof h) return set_err(SIM_ERR_BADARG, "checkpoint too short");
+    memcpy(&h, blob, sizeof h);
+    const RegLayout& L = b->nl->layout;
+    DevState& S = b->S;
+    if (h.magic != kMagic || h.version != 1 || h.n_reg != b->nl->nl.reg_w.size() || h.I != S.I ||
+        h.mode != uint64_t(b->mode) || h.n_mem_words != b->nl->mem_word_off.back())
+        return set_err(SIM_ERR_BADARG, "checkpoint does not match this batch");
+    size_t nb = size_t(L.count[RC_BIT]) * S.bit_stride * 4, n32 = size_t(L.count[RC_W32]) * S.I * 4,
+           n64 = size_t(L.count[RC_W64]) * S.I * 8, nm = b->mem.n, nmd = b->mem_dig.n, nh = b->h_hold_val.size();
+    if (len != sizeof h + nb + n32 + n64 + nm + nmd + nh * 9) return set_err(SIM_ERR_BADARG, "checkpoint size mismatch");
+    const uint32_t par = uint32_t(h.cycle & 1);
+    const char* q = static_cast<const char*>(blob) + sizeof h;
+    auto h2d = [&](void* dst, size_t n) {
+        if (n && b->h2d(dst, q, n) != SIM_OK) return false;
+        q += n;
+        return true;
+    };
+    if (!h2d(S.bits[par], nb) || !h2d(S.w32[par], n32) || !h2d(S.w64[par], n64) || !h2d(S.mem, nm) || !h2d(S.mem_dig, nmd))
+        return set_err(SIM_ERR_CUDA, "restore copy failed");
+    if (nh) {
+        memcpy(b->h_hold_val.data(), q, nh * 8);
+        q += nh * 8;
+        memcpy(b->h_hold_flag.data(), q, nh);
+        if ((rc = b->h2d(b->hold_val.p, b->h_hold_val.data(), nh * 8))) return rc;
+        if ((rc = b->h2d(b->hold_flag.p, b->h_hold_flag.data(), nh))) return rc;
+        S.any_hold = std::any_of(b->h_hold_flag.begin(), b->h_hold_flag.end(), [](uint8_t f) { return f != 0; });
+    }
+    for (int k = 0; k < 2; k++)
+        if (b->rec[k].n) CUDA_TRY(cudaMemsetAsync(b->rec[k].p, 0, b->rec[k].n, b->stream));
+    b->cycle = h.cycle;
+    return SIM_OK;
+}
+
+void sim_free_blob(void* blob) { free(blob); }
+
+int sim_launch_info(sim_batch* b, uint32_t* ctas, uint32_t* warps_per_cta, uint32_t* tasks_per_cycle,
+                    uint64_t* kernels_launched) {
+    if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    if (ctas) *ctas = uint32_t(b->grid);
+    if (warps_per_cta) *warps_per_cta = uint32_t(b->warps);
+    if (tasks_per_cycle) *tasks_per_cycle = b->n_tasks;
+    if (kernels_launched) *kernels_launched = b->kernels_launched;
+    return SIM_OK;
+}
+
+int sim_debug_skip_arrival(sim_batch* b, uint32_t timeout_ms) {
+    if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    if (b->grid < 2) return set_err(SIM_ERR_STATE, "needs at least two CTAs");
+    b->skip_cta = 0;
+    b->timeout_ns = uint64_t(timeout_ms) * 1000000ULL;
+    return SIM_OK;
+}
+
+}  // extern "C"

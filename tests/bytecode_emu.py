@@ -1,0 +1,130 @@
+"""Test helper: a Python emulator of the simulator's device bytecode.
+
+Written from the instruction-set definition (the DIns layout and opcode
+list of the compiler header), not from the CUDA kernels, so that the lowered
+program (schedule steps, slot allocation, register addressing, write records)
+can be checked against the oracle on the CPU.  Registers are addressed by
+their netlist index (instruction field imm).
+"""
+import oracle
+
+D_NOP, D_LDR, D_LDI, D_CONST, D_MEMRD = 0, 1, 2, 3, 4
+D_ADD, D_SUB, D_MUL, D_AND, D_OR, D_XOR, D_SHL, D_SHR, D_EQ, D_LT = range(5, 15)
+D_MUX, D_SLICE, D_CONCAT, D_STR, D_WREC, D_COMMIT = range(15, 21)
+M64 = (1 << 64) - 1
+
+
+def mask(w):
+    return (1 << w) - 1
+
+
+class Emu:
+    def __init__(self, net_text, netlist, mode, seed=42, inst=0):
+        from pyeval import PyNet
+        self.py = PyNet(net_text)
+        self.mode = mode
+        self.seed, self.inst = seed, inst
+        if mode == "lane_op":
+            self.ins = netlist.table("s_ins")
+            self.off = netlist.table("s_off")
+            self.len = netlist.table("s_len")
+            self.nslots = netlist.table("s_slots")
+        else:
+            self.ins = netlist.table("b_ins")
+            self.off = netlist.table("b_off")
+            self.len = netlist.table("b_len")
+            self.nslots = netlist.table("b_slots")
+        self.regs, self.mems = self.py.initial_state()
+        self.cycle = 0
+        self.pending = {}           # port -> (en, addr, data) of the previous cycle
+        self.n_in = len(self.py.inputs)
+
+    def _read_mem(self, m, addr):
+        v = self.mems[m][addr]
+        for port in sorted(self.pending):
+            pm = self.py.wports[port][0]
+            en, a, d = self.pending[port]
+            if pm == m and en and a == addr:
+                v = d
+        return v
+
+    def _commit(self, m):
+        for port in sorted(self.pending):
+            en, a, d = self.pending[port]
+            if self.py.wports[port][0] == m and en:
+                self.mems[m][a] = d
+
+    def _exec(self, d, slots, nxt, recs):
+        op, w = int(d["op"]), int(d["w"])
+        S = lambda k: slots[int(d[k])]
+        if op == D_NOP:
+            return None
+        if op == D_LDR:
+            return self.regs[int(d["imm"])]
+        if op == D_LDI:
+            k = int(d["imm"])
+            return oracle.stimulus(self.seed, self.inst, self.cycle, k, self.n_in, w)
+        if op == D_CONST:
+            return int(d["imm"]) | (int(d["a"]) << 32) | (int(d["b"]) << 48)
+        if op == D_MEMRD:
+            m = int(d["imm"])
+            depth = 2 ** self.py.mems[m][0]
+            return self._read_mem(m, S("a") % depth)
+        if op == D_STR:
+            r = int(d["imm"])
+            assert nxt[r] is None, f"register {r} stored twice"
+            nxt[r] = S("a") & mask(w)
+            return None
+        if op == D_WREC:
+            port = int(d["imm"])
+            recs[port] = (S("a") != 0, S("b") & mask(int(d["x"])), S("c") & mask(w))
+            return None
+        if op == D_COMMIT:
+            if self.pending:
+                self._commit(int(d["imm"]))
+            return None
+        a, b = S("a"), S("b")
+        if op == D_MUX:
+            v = b if a != 0 else S("c")
+        elif op == D_SLICE:
+            v = a >> int(d["x"])
+        elif op == D_CONCAT:
+            v = (a << int(d["x"])) | b
+        elif op == D_SHL:
+            v = 0 if b >= 64 else (a << b) & M64
+        elif op == D_SHR:
+            v = 0 if b >= 64 else a >> b
+        else:
+            v = {D_ADD: a + b, D_SUB: a - b, D_MUL: a * b, D_AND: a & b, D_OR: a | b, D_XOR: a ^ b,
+                 D_EQ: int(a == b), D_LT: int(a < b)}[op]
+        return v & mask(w)
+
+    def step(self, order=None):
+        nxt = [None] * len(self.regs)
+        recs = {}
+        procs = order if order is not None else range(len(self.off))
+        for p in procs:
+            slots = [None] * int(self.nslots[p])
+            if self.mode == "lane_op":
+                for b in range(int(self.len[p])):
+                    row = self.ins[(int(self.off[p]) + b) * 32:(int(self.off[p]) + b + 1) * 32]
+                    outs = [(int(d["dst"]), self._exec(d, slots, nxt, recs)) for d in row]
+                    for dst, v in outs:        # all 32 lanes read before any writes
+                        if v is not None:
+                            slots[dst] = v
+            else:
+                base = int(self.off[p])
+                for i in range(int(self.len[p])):
+                    d = self.ins[base + i]
+                    v = self._exec(d, slots, nxt, recs)
+                    if v is not None:
+                        slots[int(d["dst"])] = v
+        assert all(v is not None for v in nxt), "a register got no next value"
+        self.regs = nxt
+        self.pending = recs
+        self.cycle += 1
+
+    def finish(self):
+        for m in range(len(self.mems)):
+            self._commit(m)
+        self.pending = {}

@@ -1,0 +1,51 @@
+"""The lowered bytecode, run by a Python emulator of the instruction set,
+reproduces the oracle cycle by cycle (CPU only): checks the schedule steps,
+value-slot reuse, register addressing and memory write records before any
+GPU run."""
+import random
+
+import pytest
+
+import oracle
+from bytecode_emu import Emu
+from paper_2403_04714_gb300 import netgen, sim
+from test_oracle_bruteforce import random_tiny_circuit
+
+
+def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False):
+    nl = sim.Netlist(text, mode=mode, target_processes=target, seed_partition=seed_partition)
+    emu = Emu(text, nl, mode, seed=42, inst=0)
+    ref = oracle.Sim(oracle.Net(text=text), seed=42, inst=0)
+    rng = random.Random(1)
+    n_proc = len(emu.off)
+    for t in range(cycles):
+        order = list(range(n_proc))
+        if shuffle:
+            rng.shuffle(order)
+        emu.step(order)
+        ref.run(1)
+        assert emu.regs == [int(v) for v in ref.regs()], (mode, t)
+    emu.finish()
+    for m in range(len(emu.mems)):
+        assert emu.mems[m] == [ref.mem(m, a) for a in range(len(emu.mems[m]))]
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+def test_tiny_workload(mode):
+    text = open(netgen.cached_netlist("tiny")).read()
+    run_compare(text, mode, 40, shuffle=True)
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+@pytest.mark.parametrize("seed", range(6))
+def test_random_circuits_with_memory(mode, seed):
+    text = random_tiny_circuit(seed).to_text()
+    for target in (1, 2, 4):
+        run_compare(text, mode, 25, target=target, shuffle=True)
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+def test_flat_netlist_with_rams(mode):
+    text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
+    for target, sp in ((16, 0), (40, 3)):
+        run_compare(text, mode, 30, target=target, seed_partition=sp, shuffle=True)
