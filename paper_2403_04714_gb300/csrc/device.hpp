@@ -38,6 +38,7 @@ struct DevState {
     uint64_t* ring;             // per-cycle digests [cap][n_tracked]
     const int32_t* track;       // per instance: ring column or -1
     uint64_t* mem_dig;          // running memory digest part [n_mem][I]
+    const uint64_t* rom_dig;    // digest of the memories without write ports, per instance
     uint32_t* bar;              // grid barrier words: [0] arrivals, [1] generation
     int32_t* err;               // first error code of the launch (0 = none)
     uint32_t I;                 // instances (padded to the lane-group size)

@@ -266,7 +266,10 @@ __device__ void task_lane_inst(const DevProg& P, const DevState& S, uint32_t p, 
         }
     }
 #undef SL
-    if (DIGEST && col >= 0) ring_add(S, t + 1, col, dacc);
+    if (DIGEST && col >= 0) {
+        if (p == 0) dacc += S.rom_dig[inst];    // memories without write ports never change in a step
+        ring_add(S, t + 1, col, dacc);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -336,6 +339,7 @@ __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, ui
         raw = next_raw;
     }
     if (DIGEST && col >= 0) {
+        if (p == 0 && lane == 0) dacc += S.rom_dig[inst];
         for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
         if (lane == 0) ring_add(S, t + 1, col, dacc);
     }

@@ -118,7 +118,8 @@ struct sim_batch {
     DBuf s_ins, s_off, s_len, b_ins, b_off, b_len, mport_off, mport_id, mem_lg, mem_w, mem_base, in_w, reg_cls, reg_idx,
         mem_word_off;
     // state
-    DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, bar, err, t0_dev, scratch;
+    DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, rom_dig, bar, err, t0_dev,
+        scratch;
     DevProg P{};
     DevState S{};
     std::vector<uint8_t> h_hold_flag;     // host mirror
@@ -438,6 +439,13 @@ int init_state(sim_batch* b) {
         }
         if ((rc = upload(b->mem_dig, md, st))) return rc;
         S.mem_dig = b->mem_dig.as<uint64_t>();
+        // memories without write ports: their digest term is added each cycle by process 0
+        std::vector<uint64_t> rd(I, 0);
+        for (size_t m = 0; m < nl.mem_lg.size(); m++)
+            if (nl.mem_ports[m].empty())
+                for (uint64_t i = 0; i < I; i++) rd[i] += md[m * I + i];
+        if ((rc = upload(b->rom_dig, rd, st))) return rc;
+        S.rom_dig = b->rom_dig.as<uint64_t>();
     }
     if ((rc = b->bar.alloc(16)) || (rc = b->err.alloc(16)) || (rc = b->t0_dev.alloc(8))) return rc;
     S.bar = b->bar.as<uint32_t>();
@@ -762,8 +770,16 @@ int sim_poke_mem(sim_batch* b, uint32_t inst, uint32_t mem, uint64_t addr, uint6
     if ((rc = b->h2d(cell, &value, 8))) return rc;
     uint64_t* mdp = b->S.mem_dig + size_t(mem) * b->I + inst;
     if ((rc = b->d2h(&md, mdp, 8))) return rc;
-    md += host_mix64(mem_hash(mem, addr) ^ value) - host_mix64(mem_hash(mem, addr) ^ old);
+    uint64_t delta = host_mix64(mem_hash(mem, addr) ^ value) - host_mix64(mem_hash(mem, addr) ^ old);
+    md += delta;
     if ((rc = b->h2d(mdp, &md, 8))) return rc;
+    if (nl.mem_ports[mem].empty()) {
+        uint64_t rd;
+        uint64_t* rdp = b->rom_dig.as<uint64_t>() + inst;
+        if ((rc = b->d2h(&rd, rdp, 8))) return rc;
+        rd += delta;
+        if ((rc = b->h2d(rdp, &rd, 8))) return rc;
+    }
     return SIM_OK;
 }
 

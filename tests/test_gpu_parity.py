@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 def oracle_digests(text_or_path, seed, inst, n, is_path=False):
     net = oracle.Net(path=text_or_path) if is_path else oracle.Net(text=text_or_path)
     s = oracle.Sim(net, seed, inst)
-    return np.concatenate([[s.digest()], s.run(n, digests=True)]).astype(np.uint64), s
+    return np.concatenate([np.array([s.digest()], dtype=np.uint64), s.run(n, digests=True)]), s
 
 
 def oracle_many(text, seed, insts, n):
