@@ -126,6 +126,10 @@ void sim_netlist_destroy(sim_netlist *nl);
  *  10 register storage class (u8: 0 1-bit, 1 <=32-bit, 2 <=64-bit)
  *  11 register index within its class (u32)
  *  12 LANE_OP slot count of each process (u32)    13 LANE_INST slot count (u32)
+ *  14 LANE_OP compact programs kept in shared memory (u32 words: per process
+ *     a step table, first instruction | count << 16, padded to 4 words, then
+ *     the 16-byte instructions)                    15 first word of each (u32)
+ *  16 words of each (u32)
  * Errors: BADARG. */
 int sim_netlist_table(const sim_netlist *nl, int32_t which, void *out, size_t *bytes);
 

@@ -755,6 +755,8 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
     out.s_off.resize(NP);
     out.s_len.resize(NP);
     out.s_slots.resize(NP);
+    out.c_off.resize(NP);
+    out.c_size.resize(NP);
     out.b_off.resize(NP);
     out.b_len.resize(NP);
     out.b_slots.resize(NP);
@@ -916,6 +918,26 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             }
             out.s_len[p] = nb;
             out.s_slots[p] = std::max<uint32_t>(1, A.next);
+            // compact copy: bundle table, then the occupied lanes of each row
+            std::vector<uint32_t> count(nb, 0);
+            for (size_t k = 0; k < items.size(); k++) count[bundle[k]]++;
+            const uint32_t table_words = (nb + 3) / 4 * 4;
+            out.c_off[p] = uint32_t(out.c_words.size());
+            std::vector<uint32_t> prog(table_words, 0);
+            uint32_t first = 0;
+            for (uint32_t b = 0; b < nb; b++) {
+                prog[b] = first | (count[b] << 16);
+                const DIns* row = &out.s_ins[(size_t(out.s_off[p]) + b) * 32];
+                for (uint32_t l = 0; l < count[b]; l++) {
+                    uint32_t w[4];
+                    memcpy(w, &row[l], 16);
+                    prog.insert(prog.end(), w, w + 4);
+                }
+                first += count[b];
+            }
+            if (first > 0xffff) { err = "process has too many instructions for one program"; return SIM_ERR_CAPACITY; }
+            out.c_size[p] = uint32_t(prog.size());
+            out.c_words.insert(out.c_words.end(), prog.begin(), prog.end());
             if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
         }
         // ---- LANE_INST: sequential list in depth-first post-order from each

@@ -113,6 +113,12 @@ struct Lowered {
     std::vector<uint32_t> s_off;      // per process: first bundle
     std::vector<uint32_t> s_len;      // per process: bundle count
     std::vector<uint32_t> s_slots;    // per process: slot count
+    // LANE_OP compact program (what a warp keeps in shared memory): per
+    // process a bundle table (first instruction | count << 16, one word per
+    // step) followed by the step instructions without padding, 16-byte aligned
+    std::vector<uint32_t> c_words;    // packed programs, 32-bit words
+    std::vector<uint32_t> c_off;      // per process: first word (multiple of 4)
+    std::vector<uint32_t> c_size;     // per process: words (multiple of 4)
     // LANE_INST: linear instruction list
     std::vector<DIns> b_ins;
     std::vector<uint32_t> b_off, b_len, b_slots;

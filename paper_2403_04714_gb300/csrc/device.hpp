@@ -11,6 +11,9 @@ struct DevProg {
     const DIns* s_ins;          // LANE_OP bundles (32 instructions per row)
     const uint32_t* s_off;
     const uint32_t* s_len;
+    const uint32_t* c_words;    // LANE_OP compact programs (step table + instructions)
+    const uint32_t* c_off;      // per process: first word
+    const uint32_t* c_size;     // per process: words (multiple of 4)
     const DIns* b_ins;          // LANE_INST linear streams
     const uint32_t* b_off;
     const uint32_t* b_len;
@@ -58,7 +61,8 @@ struct LaunchArgs {
     int32_t skip_cta;           // testing: this CTA skips its first barrier arrival (-1 none)
     uint64_t timeout_ns;        // barrier wait limit
     uint32_t warps_per_cta;
-    uint32_t slot_words;        // per-warp slot area in 64-bit words
+    uint32_t slot_words;        // per-warp slot area in 64-bit words (even)
+    uint32_t prog_words;        // per-warp resident program area in 32-bit words (0 = read from global)
     uint32_t n_tasks;           // processes x instance groups
     uint32_t group;             // instances per task (1 LANE_OP, 32 LANE_INST)
 };

@@ -276,9 +276,73 @@ __device__ void task_lane_inst(const DevProg& P, const DevState& S, uint32_t p, 
 // LANE_OP: one warp, one process, one instance; lanes run a 32-wide step.
 // ---------------------------------------------------------------------------
 template <bool DIGEST>
+__device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, const DevState& S, uint32_t inst, uint64_t t,
+                                             uint64_t key, int32_t col, bool pending, uint64_t* __restrict__ sl,
+                                             uint64_t& dacc) {
+    const uint32_t par = uint32_t(t & 1), nxt = par ^ 1;
+    switch (d.op) {
+    case D_NOP:
+        break;
+    case D_LDR:
+        sl[d.dst] = load_reg(S, par, d.c, d.b | (d.x << 16), inst);
+        break;
+    case D_LDI:
+        sl[d.dst] = stimulus(P, S, key, d.imm, inst, t, d.w);
+        break;
+    case D_CONST:
+        sl[d.dst] = (uint64_t)d.imm | ((uint64_t)d.a << 32) | ((uint64_t)d.b << 48);
+        break;
+    case D_MEMRD: {
+        uint64_t addr = sl[d.a] & ((1ULL << P.mem_lg[d.imm]) - 1);
+        sl[d.dst] = mem_read(P, S, d.imm, addr, inst, nxt, pending);
+        break;
+    }
+    case D_STR: {
+        uint64_t v = sl[d.a] & wmask(d.w);
+        uint32_t idx = d.b | (d.x << 16);
+        if (d.c == RC_W64) S.w64[nxt][(uint64_t)idx * S.I + inst] = v;
+        else if (d.c == RC_W32) S.w32[nxt][(uint64_t)idx * S.I + inst] = uint32_t(v);
+        else S.bits[nxt][(uint64_t)idx * S.bit_stride + inst] = uint32_t(v);   // pack == 1
+        if (DIGEST && col >= 0) dacc += mix64(((uint64_t)d.imm * kGamma + 1ULL) ^ v);
+        break;
+    }
+    case D_WREC: {
+        uint64_t en = sl[d.a] != 0;
+        uint64_t addr = sl[d.b] & ((1ULL << d.x) - 1);
+        uint64_t data = sl[d.c] & wmask(d.w);
+        uint64_t* r = S.rec[par] + ((uint64_t)d.imm * S.I + inst) * 2;
+        r[0] = en ? ((1ULL << 63) | addr) : 0;
+        r[1] = data;
+        break;
+    }
+    case D_COMMIT:
+        if (pending) {
+            uint64_t delta = mem_commit(P, S, d.imm, inst, nxt, DIGEST && col >= 0);
+            if (DIGEST) mem_digest_update(S, d.imm, inst, t, delta);
+        }
+        break;
+    case D_MUX:
+        sl[d.dst] = alu(D_MUX, sl[d.a], sl[d.b], sl[d.c], 0) & wmask(d.w);
+        break;
+    default:
+        sl[d.dst] = alu(d.op, sl[d.a], sl[d.b], 0, d.x) & wmask(d.w);
+    }
+}
+
+template <bool DIGEST>
+__device__ __forceinline__ void finish_lane_op(const DevState& S, uint32_t p, uint32_t inst, uint64_t t, int32_t col,
+                                               uint32_t lane, uint64_t dacc) {
+    if (DIGEST && col >= 0) {
+        if (p == 0 && lane == 0) dacc += S.rom_dig[inst];    // memories without write ports
+        for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
+        if (lane == 0) ring_add(S, t + 1, col, dacc);
+    }
+}
+
+// Program rows read from global memory (32-wide padded rows).
+template <bool DIGEST>
 __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t, bool pending,
                              uint64_t* __restrict__ sl, uint32_t lane) {
-    const uint32_t par = uint32_t(t & 1), nxt = par ^ 1;
     const uint64_t key = S.key[inst];
     const int32_t col = DIGEST ? S.track[inst] : -1;
     uint64_t dacc = 0;
@@ -287,62 +351,33 @@ __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, ui
     uint4 raw = nb ? ld_ins(bp) : make_uint4(0, 0, 0, 0);
     for (uint32_t b = 0; b < nb; b++) {
         uint4 next_raw = (b + 1 < nb) ? ld_ins(bp + (uint64_t)(b + 1) * 32) : make_uint4(0, 0, 0, 0);
-        Dec d = decode(raw);
-        switch (d.op) {
-        case D_NOP:
-            break;
-        case D_LDR:
-            sl[d.dst] = load_reg(S, par, d.c, d.b | (d.x << 16), inst);
-            break;
-        case D_LDI:
-            sl[d.dst] = stimulus(P, S, key, d.imm, inst, t, d.w);
-            break;
-        case D_CONST:
-            sl[d.dst] = (uint64_t)d.imm | ((uint64_t)d.a << 32) | ((uint64_t)d.b << 48);
-            break;
-        case D_MEMRD: {
-            uint64_t addr = sl[d.a] & ((1ULL << P.mem_lg[d.imm]) - 1);
-            sl[d.dst] = mem_read(P, S, d.imm, addr, inst, nxt, pending);
-            break;
-        }
-        case D_STR: {
-            uint64_t v = sl[d.a] & wmask(d.w);
-            uint32_t idx = d.b | (d.x << 16);
-            if (d.c == RC_W64) S.w64[nxt][(uint64_t)idx * S.I + inst] = v;
-            else if (d.c == RC_W32) S.w32[nxt][(uint64_t)idx * S.I + inst] = uint32_t(v);
-            else S.bits[nxt][(uint64_t)idx * S.bit_stride + inst] = uint32_t(v);   // pack == 1
-            if (DIGEST && col >= 0) dacc += mix64(((uint64_t)d.imm * kGamma + 1ULL) ^ v);
-            break;
-        }
-        case D_WREC: {
-            uint64_t en = sl[d.a] != 0;
-            uint64_t addr = sl[d.b] & ((1ULL << d.x) - 1);
-            uint64_t data = sl[d.c] & wmask(d.w);
-            uint64_t* r = S.rec[par] + ((uint64_t)d.imm * S.I + inst) * 2;
-            r[0] = en ? ((1ULL << 63) | addr) : 0;
-            r[1] = data;
-            break;
-        }
-        case D_COMMIT:
-            if (pending) {
-                uint64_t delta = mem_commit(P, S, d.imm, inst, nxt, DIGEST && col >= 0);
-                if (DIGEST) mem_digest_update(S, d.imm, inst, t, delta);
-            }
-            break;
-        case D_MUX:
-            sl[d.dst] = alu(D_MUX, sl[d.a], sl[d.b], sl[d.c], 0) & wmask(d.w);
-            break;
-        default:
-            sl[d.dst] = alu(d.op, sl[d.a], sl[d.b], 0, d.x) & wmask(d.w);
-        }
+        exec_lane_op<DIGEST>(decode(raw), P, S, inst, t, key, col, pending, sl, dacc);
         __syncwarp();
         raw = next_raw;
     }
-    if (DIGEST && col >= 0) {
-        if (p == 0 && lane == 0) dacc += S.rom_dig[inst];
-        for (int o = 16; o; o >>= 1) dacc += __shfl_xor_sync(0xffffffffu, dacc, o);
-        if (lane == 0) ring_add(S, t + 1, col, dacc);
+    finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
+}
+
+// Program resident in shared memory: `prog` holds the step table (first
+// instruction | count << 16) followed by the instructions, 16-byte aligned.
+template <bool DIGEST>
+__device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t,
+                                 bool pending, uint64_t* __restrict__ sl, const uint32_t* __restrict__ prog,
+                                 uint32_t lane) {
+    const uint64_t key = S.key[inst];
+    const int32_t col = DIGEST ? S.track[inst] : -1;
+    uint64_t dacc = 0;
+    const uint32_t nb = P.s_len[p];
+    const uint4* ins = reinterpret_cast<const uint4*>(prog + ((nb + 3) & ~3u));
+    uint32_t e = nb ? prog[0] : 0;
+    for (uint32_t b = 0; b < nb; b++) {
+        const uint32_t e_next = b + 1 < nb ? prog[b + 1] : 0;
+        const uint32_t first = e & 0xffff, cnt = e >> 16;
+        if (lane < cnt) exec_lane_op<DIGEST>(decode(ins[first + lane]), P, S, inst, t, key, col, pending, sl, dacc);
+        __syncwarp();
+        e = e_next;
     }
+    finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
 
 // Apply the last cycle's write records after the final barrier of a launch
@@ -361,20 +396,41 @@ __device__ void final_commit(const DevProg& P, const DevState& S, uint64_t t_end
 
 template <int MODE, bool DIGEST>
 __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchArgs A) {
-    extern __shared__ uint64_t smem[];
+    extern __shared__ __align__(16) uint64_t smem[];
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t warp = blockIdx.x * A.warps_per_cta + wib;
     const uint32_t tw = gridDim.x * A.warps_per_cta;
-    uint64_t* sl = smem + (uint64_t)wib * A.slot_words;
-    uint32_t gen = 0;
+    uint64_t* sl = smem + (uint64_t)wib * (A.slot_words + A.prog_words / 2);
+    uint32_t* prog = reinterpret_cast<uint32_t*>(sl + A.slot_words);
+    const bool resident = MODE == SIM_MODE_LANE_OP && A.prog_words > 0;
+    if (resident) {
+        // copy the compact programs of the processes this warp owns (p = warp + k*tw)
+        uint32_t off = 0;
+        for (uint32_t p = warp; p < P.n_proc; p += tw) {
+            const uint4* src = reinterpret_cast<const uint4*>(P.c_words + P.c_off[p]);
+            uint4* dst = reinterpret_cast<uint4*>(prog + off);
+            for (uint32_t k = lane; k < P.c_size[p] / 4; k += 32) dst[k] = __ldg(src + k);
+            off += P.c_size[p];
+        }
+        __syncwarp();
+    }
     const uint64_t t_base = A.t0_dev ? *A.t0_dev + A.t0 : A.t0;
+    uint32_t gen = 0;
     for (uint32_t c = 0; c < A.n; c++) {
         const uint64_t t = t_base + c;
         const bool pending = c > 0 || A.pending_first;
-        for (uint32_t task = warp; task < A.n_tasks; task += tw) {
-            uint32_t p = task % P.n_proc, g = task / P.n_proc;
-            if (MODE == SIM_MODE_LANE_INST) task_lane_inst<DIGEST>(P, S, p, g, t, pending, sl, lane);
-            else task_lane_op<DIGEST>(P, S, p, g, t, pending, sl, lane);
+        if (resident) {
+            uint32_t off = 0;
+            for (uint32_t p = warp; p < P.n_proc; p += tw) {
+                for (uint32_t g = 0; g < S.I; g++) task_lane_op_res<DIGEST>(P, S, p, g, t, pending, sl, prog + off, lane);
+                off += P.c_size[p];
+            }
+        } else {
+            for (uint32_t task = warp; task < A.n_tasks; task += tw) {
+                uint32_t p = task % P.n_proc, g = task / P.n_proc;
+                if (MODE == SIM_MODE_LANE_INST) task_lane_inst<DIGEST>(P, S, p, g, t, pending, sl, lane);
+                else task_lane_op<DIGEST>(P, S, p, g, t, pending, sl, lane);
+            }
         }
         if (A.grid_sync) {
             bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;

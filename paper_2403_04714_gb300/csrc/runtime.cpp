@@ -115,8 +115,8 @@ struct sim_batch {
     uint32_t n_inst = 0, I = 0;
     uint64_t seed = 0, cycle = 0;
     // program tables
-    DBuf s_ins, s_off, s_len, b_ins, b_off, b_len, mport_off, mport_id, mem_lg, mem_w, mem_base, in_w, reg_cls, reg_idx,
-        mem_word_off;
+    DBuf s_ins, s_off, s_len, c_words, c_off, c_size, b_ins, b_off, b_len, mport_off, mport_id, mem_lg, mem_w, mem_base,
+        in_w, reg_cls, reg_idx, mem_word_off;
     // state
     DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, rom_dig, bar, err, t0_dev,
         scratch;
@@ -129,7 +129,7 @@ struct sim_batch {
     // launch geometry
     int threads = 256, warps = 8, grid = 0, max_grid = 0;
     size_t smem = 0;
-    uint32_t slot_words = 0, n_tasks = 0;
+    uint32_t slot_words = 0, prog_words = 0, n_tasks = 0;
     uint64_t kernels_launched = 0;
     int32_t skip_cta = -1;
     uint64_t timeout_ns = 2000000000ULL;
@@ -276,6 +276,9 @@ int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* b
     case 11: pick(nl->layout.idx); break;
     case 12: pick(L.s_slots); break;
     case 13: pick(L.b_slots); break;
+    case 14: pick(L.c_words); break;
+    case 15: pick(L.c_off); break;
+    case 16: pick(L.c_size); break;
     default: return set_err(SIM_ERR_BADARG, "unknown table");
     }
     if (out) memcpy(out, src, std::min(n, *bytes));
@@ -287,29 +290,64 @@ int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* b
 
 namespace {
 
-// Choose warps per CTA and grid for a batch (both lane mappings).
+// Largest sum of compact-program sizes over the processes one warp owns
+// (process p belongs to warp p mod total_warps), in 32-bit words.
+uint32_t resident_words(const Lowered& L, uint32_t total_warps) {
+    std::vector<uint64_t> per(std::min<size_t>(total_warps, L.c_size.size()), 0);
+    for (size_t p = 0; p < L.c_size.size(); p++) per[p % per.size()] += L.c_size[p];
+    uint64_t mx = 0;
+    for (uint64_t v : per) mx = std::max(mx, v);
+    return uint32_t(std::min<uint64_t>(mx, 0xffffffffu));
+}
+
+// Choose warps per CTA and grid for a batch (both lane mappings).  LANE_OP
+// keeps each warp's programs resident in shared memory when they fit.
 int plan_launch(sim_batch* b) {
     const Lowered& L = b->nl->low;
     const int sms = sm_count();
     const size_t smem_cap = 220 * 1024;
+    const uint32_t n_proc = uint32_t(b->nl->part.procs.size());
     if (b->mode == SIM_MODE_LANE_INST) {
         b->slot_words = L.max_b_slots * 32;
-        b->n_tasks = uint32_t(b->nl->part.procs.size()) * (b->I / 32);
+        b->n_tasks = n_proc * (b->I / 32);
     } else {
-        b->slot_words = L.max_s_slots;
-        b->n_tasks = uint32_t(b->nl->part.procs.size()) * b->I;
+        b->slot_words = (L.max_s_slots + 1) & ~1u;
+        b->n_tasks = n_proc * b->I;
     }
-    size_t per_warp = size_t(b->slot_words) * 8;
-    if (per_warp > smem_cap)
-        return set_err(SIM_ERR_CAPACITY, "a process needs " + std::to_string(per_warp) +
+    size_t slot_bytes = size_t(b->slot_words) * 8;
+    if (slot_bytes > smem_cap)
+        return set_err(SIM_ERR_CAPACITY, "a process needs " + std::to_string(slot_bytes) +
                                              " bytes of value slots per warp (limit " + std::to_string(smem_cap) + ")");
     int warps = b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8;
-    while (warps > 1 && size_t(warps) * per_warp > smem_cap) warps /= 2;
+    while (warps > 1 && size_t(warps) * slot_bytes > smem_cap) warps /= 2;
     b->warps = warps;
     b->threads = warps * 32;
-    b->smem = size_t(warps) * per_warp;
-    CUDA_TRY(prepare_cycles_kernel(b->mode, b->smem));
+    b->prog_words = 0;
     int occ = 0;
+    if (b->mode == SIM_MODE_LANE_OP) {
+        // one process per warp when the grid allows it; re-plan with the
+        // smaller grid if the resident programs lower occupancy
+        uint32_t grid = (n_proc + warps - 1) / warps;
+        for (int iter = 0; iter < 3; iter++) {
+            uint32_t pw = (resident_words(L, grid * warps) + 3) & ~3u;
+            size_t smem = size_t(warps) * (slot_bytes + size_t(pw) * 4);
+            if (smem > smem_cap) break;
+            CUDA_TRY(prepare_cycles_kernel(b->mode, smem));
+            CUDA_TRY(occupancy_cycles(b->mode, b->threads, smem, &occ));
+            if (occ < 1) break;
+            uint32_t max_grid = uint32_t(occ * sms);
+            if (grid <= max_grid) {
+                b->prog_words = pw;
+                b->smem = smem;
+                b->max_grid = int(max_grid);
+                b->grid = int(grid);
+                return SIM_OK;
+            }
+            grid = max_grid;
+        }
+    }
+    b->smem = size_t(warps) * slot_bytes;
+    CUDA_TRY(prepare_cycles_kernel(b->mode, b->smem));
     CUDA_TRY(occupancy_cycles(b->mode, b->threads, b->smem, &occ));
     if (occ < 1) return set_err(SIM_ERR_CAPACITY, "kernel does not fit on an SM");
     b->max_grid = occ * sms;
@@ -327,6 +365,8 @@ int upload_program(sim_batch* b) {
     std::vector<uint64_t> mem_base(nl.mem_lg.size());
     for (size_t m = 0; m < nl.mem_lg.size(); m++) mem_base[m] = h->mem_word_off[m] * b->I;
     if ((rc = upload(b->s_ins, L.s_ins, st)) || (rc = upload(b->s_off, L.s_off, st)) || (rc = upload(b->s_len, L.s_len, st)) ||
+        (rc = upload(b->c_words, L.c_words, st)) || (rc = upload(b->c_off, L.c_off, st)) ||
+        (rc = upload(b->c_size, L.c_size, st)) ||
         (rc = upload(b->b_ins, L.b_ins, st)) || (rc = upload(b->b_off, L.b_off, st)) || (rc = upload(b->b_len, L.b_len, st)) ||
         (rc = upload(b->mport_off, h->mport_off, st)) || (rc = upload(b->mport_id, h->mport_id, st)) ||
         (rc = upload(b->mem_lg, nl.mem_lg, st)) || (rc = upload(b->mem_w, nl.mem_w, st)) ||
@@ -338,6 +378,9 @@ int upload_program(sim_batch* b) {
     P.s_ins = b->s_ins.as<DIns>();
     P.s_off = b->s_off.as<uint32_t>();
     P.s_len = b->s_len.as<uint32_t>();
+    P.c_words = b->c_words.as<uint32_t>();
+    P.c_off = b->c_off.as<uint32_t>();
+    P.c_size = b->c_size.as<uint32_t>();
     P.b_ins = b->b_ins.as<DIns>();
     P.b_off = b->b_off.as<uint32_t>();
     P.b_len = b->b_len.as<uint32_t>();
@@ -514,6 +557,7 @@ LaunchArgs base_args(sim_batch* b) {
     A.timeout_ns = b->timeout_ns;
     A.warps_per_cta = uint32_t(b->warps);
     A.slot_words = b->slot_words;
+    A.prog_words = b->prog_words;
     A.n_tasks = b->n_tasks;
     A.group = b->mode == SIM_MODE_LANE_INST ? 32 : 1;
     return A;
@@ -547,11 +591,18 @@ int step_persistent(sim_batch* b, uint64_t n) {
     return SIM_OK;
 }
 
+// Launch-per-cycle grid: one warp per task, except that resident LANE_OP
+// programs were laid out for the planned grid.
+int per_cycle_grid(sim_batch* b) {
+    if (b->prog_words) return b->grid;
+    return std::max(1, int((b->n_tasks + b->warps - 1) / b->warps));
+}
+
 int step_per_cycle(sim_batch* b, uint64_t n) {
     LaunchArgs A = base_args(b);
     A.n = 1;
     A.grid_sync = 0;
-    int grid = std::max(1, int((b->n_tasks + b->warps - 1) / b->warps));
+    int grid = per_cycle_grid(b);
     for (uint64_t k = 0; k < n; k++) {
         A.t0 = b->cycle + k;
         A.pending_first = k > 0;
@@ -577,7 +628,7 @@ int step_graph(sim_batch* b, uint64_t n) {
         A.t0_dev = b->t0_dev.as<uint64_t>();
         A.n = 1;
         A.grid_sync = 0;
-        int grid = std::max(1, int((b->n_tasks + b->warps - 1) / b->warps));
+        int grid = per_cycle_grid(b);
         cudaError_t e = cudaSuccess;
         for (uint32_t k = 0; k < chunk && e == cudaSuccess; k++) {
             A.t0 = k;
@@ -1008,3 +1059,4 @@ int sim_debug_skip_arrival(sim_batch* b, uint32_t timeout_ms) {
 }
 
 }  // extern "C"
+

@@ -93,7 +93,8 @@ TABLES = {"s_ins": (0, None), "s_off": (1, np.uint32), "s_len": (2, np.uint32), 
           "b_off": (4, np.uint32), "b_len": (5, np.uint32), "fiber_proc": (6, np.int32),
           "fiber_sink": (7, np.int32), "fiber_cost": (8, np.uint64), "proc_cost": (9, np.uint64),
           "reg_cls": (10, np.uint8), "reg_idx": (11, np.uint32), "s_slots": (12, np.uint32),
-          "b_slots": (13, np.uint32)}
+          "b_slots": (13, np.uint32), "c_words": (14, np.uint32), "c_off": (15, np.uint32),
+          "c_size": (16, np.uint32)}
 # one 16-byte instruction of the device bytecode
 DINS = np.dtype([("op", np.uint8), ("w", np.uint8), ("dst", np.uint16), ("a", np.uint16), ("b", np.uint16),
                  ("c", np.uint16), ("x", np.uint16), ("imm", np.uint32)])

@@ -24,7 +24,31 @@ class Emu:
         self.py = PyNet(net_text)
         self.mode = mode
         self.seed, self.inst = seed, inst
-        if mode == "lane_op":
+        if mode == "lane_op_compact":
+            # rebuild 32-wide rows from the shared-memory program format
+            words = netlist.table("c_words")
+            c_off, c_size = netlist.table("c_off"), netlist.table("c_size")
+            nb_all = netlist.table("s_len")
+            rows = []
+            self.off = []
+            import numpy as np
+            from paper_2403_04714_gb300.sim import DINS
+            for p in range(len(c_off)):
+                prog = words[int(c_off[p]):int(c_off[p]) + int(c_size[p])]
+                nb = int(nb_all[p])
+                table = prog[:nb]
+                ins = prog[(nb + 3) // 4 * 4:].copy().view(DINS)
+                self.off.append(len(rows) // 32)
+                for e in table:
+                    first, cnt = int(e) & 0xffff, int(e) >> 16
+                    row = np.zeros(32, dtype=DINS)
+                    row[:cnt] = ins[first:first + cnt]
+                    rows.extend(row)
+            self.ins = np.array(rows, dtype=DINS)
+            self.len = nb_all
+            self.nslots = netlist.table("s_slots")
+            mode = "lane_op"
+        elif mode == "lane_op":
             self.ins = netlist.table("s_ins")
             self.off = netlist.table("s_off")
             self.len = netlist.table("s_len")
@@ -34,6 +58,7 @@ class Emu:
             self.off = netlist.table("b_off")
             self.len = netlist.table("b_len")
             self.nslots = netlist.table("b_slots")
+        self.mode = mode
         self.regs, self.mems = self.py.initial_state()
         self.cycle = 0
         self.pending = {}           # port -> (en, addr, data) of the previous cycle

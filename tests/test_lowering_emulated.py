@@ -13,7 +13,7 @@ from test_oracle_bruteforce import random_tiny_circuit
 
 
 def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False):
-    nl = sim.Netlist(text, mode=mode, target_processes=target, seed_partition=seed_partition)
+    nl = sim.Netlist(text, mode=mode.replace("_compact", ""), target_processes=target, seed_partition=seed_partition)
     emu = Emu(text, nl, mode, seed=42, inst=0)
     ref = oracle.Sim(oracle.Net(text=text), seed=42, inst=0)
     rng = random.Random(1)
@@ -30,13 +30,13 @@ def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False):
         assert emu.mems[m] == [ref.mem(m, a) for a in range(len(emu.mems[m]))]
 
 
-@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+@pytest.mark.parametrize("mode", ["lane_op", "lane_op_compact", "lane_inst"])
 def test_tiny_workload(mode):
     text = open(netgen.cached_netlist("tiny")).read()
     run_compare(text, mode, 40, shuffle=True)
 
 
-@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+@pytest.mark.parametrize("mode", ["lane_op", "lane_op_compact", "lane_inst"])
 @pytest.mark.parametrize("seed", range(6))
 def test_random_circuits_with_memory(mode, seed):
     text = random_tiny_circuit(seed).to_text()
