@@ -166,6 +166,25 @@ int sim_cycle(sim_batch *b, uint64_t *out);
  * mix = SplitMix64 output function.  out holds n_inst values. */
 int sim_state_digests(sim_batch *b, uint64_t *out);
 
+/* The same digests as sim_state_digests, for callers that cannot let the
+ * library allocate device memory (an embedding host that owns every device
+ * byte through its own pool, or a latency-critical loop that must not pay
+ * the device-wide synchronisation of cudaMalloc/cudaFree).  The paper has
+ * no counterpart: this is an interface choice of this library.
+ *   - No cudaMalloc, cudaFree or other allocating call is made.  The
+ *     per-instance accumulator is a fixed 512 KiB device array inside the
+ *     library (at most 65536 instances, padded count); larger batches get
+ *     SIM_ERR_CAPACITY.  Every GPU that loads the library keeps that array
+ *     until the process exits.
+ *   - `out` receives n_inst digests; it may be device memory or host memory
+ *     (it is written with cudaMemcpyDefault).  The call synchronises.
+ *   - The first call on a device looks up the array's device address for
+ *     that device (with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     threads, other streams) race and may return wrong sums. */
+int sim_state_digests_noalloc(sim_batch *b, uint64_t *out);
+
 /* Per-cycle digests (ring of sim_config.digest_capacity cycles) are kept for
  * the instances listed here (default: instance 0).  Call before sim_step. */
 int sim_track_digests(sim_batch *b, const uint32_t *insts, uint32_t n);

@@ -1060,3 +1060,25 @@ int sim_debug_skip_arrival(sim_batch* b, uint32_t timeout_ms) {
 
 }  // extern "C"
 
+// ---- internal views for noalloc.cu -------------------------------------------
+namespace rtl {
+
+int set_error(int code, const std::string& msg) { return set_err(code, msg); }
+
+int batch_views(sim_batch* b, DevProg* P, DevState* S, const uint64_t** mem_word_off, uint64_t* mem_words, uint32_t* I,
+                uint32_t* n_inst, uint32_t* par, cudaStream_t* stream) {
+    if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    *P = b->P;
+    *S = b->S;
+    *mem_word_off = b->mem_word_off.as<uint64_t>();
+    *mem_words = b->nl->mem_word_off.back();
+    *I = b->I;
+    *n_inst = b->n_inst;
+    *par = uint32_t(b->cycle & 1);
+    *stream = b->stream;
+    return SIM_OK;
+}
+
+int batch_sync(sim_batch* b) { return sim_sync(b); }
+
+}  // namespace rtl

@@ -87,6 +87,7 @@ EXPORTS = {
     "sim_debug_skip_arrival": (C.c_int, [C.c_void_p, C.c_uint32]),
     "sim_last_error": (C.c_char_p, []),
     "sim_netlist_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "sim_state_digests_noalloc": (C.c_int, [C.c_void_p, C.c_void_p]),
 }
 
 TABLES = {"s_ins": (0, None), "s_off": (1, np.uint32), "s_len": (2, np.uint32), "b_ins": (3, None),
@@ -261,6 +262,11 @@ class Batch:
         out = np.zeros(self.n_inst, dtype=np.uint64)
         _check(lib().sim_state_digests(self._h, out.ctypes.data))
         return out
+
+    def state_digests_noalloc(self, out_ptr: int):
+        """sim_state_digests_noalloc: digests into caller memory (device or host
+        pointer, n_inst 64-bit words) with no allocation inside the library."""
+        _check(lib().sim_state_digests_noalloc(self._h, C.c_void_p(out_ptr)))
 
     def track_digests(self, insts):
         arr = (C.c_uint32 * len(insts))(*insts)
