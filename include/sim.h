@@ -213,6 +213,62 @@ int sim_launch_info(sim_batch *b, uint32_t *ctas, uint32_t *warps_per_cta, uint3
  * returns SIM_ERR_TIMEOUT.  No fault, trap or unbounded wait is involved. */
 int sim_debug_skip_arrival(sim_batch *b, uint32_t timeout_ms);
 
+/* ---- serving: continuous batching of simulation jobs ---------------------
+ * A server keeps one instance pool per netlist in device memory.  Jobs of
+ * the same netlist share the pool's launches (each job's instances occupy a
+ * run of slots and count cycles from their admission); pools of different
+ * netlists step concurrently on their own streams.  A job is admitted when
+ * its pool has free slots, or when a new pool fits under hbm_cap_bytes
+ * (idle pools are released to make room); otherwise it waits in arrival
+ * order without blocking jobs of other netlists.  Finished jobs free their
+ * slots at the next step boundary.  A job's results (per-instance state
+ * digests) are identical to the same instances run alone with
+ * sim_create_instances(netlist, n_inst, seed) and sim_step(n_cycles). */
+typedef struct sim_server sim_server;
+enum { SIM_JOB_QUEUED = 0, SIM_JOB_RUNNING = 1, SIM_JOB_DONE = 2, SIM_JOB_FAILED = 3 };
+
+typedef struct sim_server_config {
+    uint32_t struct_size;       /* sizeof(sim_server_config) */
+    uint32_t pool_slots;        /* instance slots per pool (default 1024) */
+    uint64_t hbm_cap_bytes;     /* device-memory cap for all pools (default 150 GiB) */
+    uint32_t chunk_cycles;      /* cycles per pool step (default 1000) */
+    uint32_t reserved[7];
+} sim_server_config;
+
+typedef struct sim_job {
+    sim_netlist *netlist;       /* must stay alive until the job is done */
+    uint32_t n_inst;            /* instances 0..n_inst-1 of `seed` */
+    uint64_t seed;
+    uint64_t n_cycles;
+} sim_job;
+
+typedef struct sim_job_status {
+    int32_t state;              /* SIM_JOB_* */
+    uint32_t n_inst;
+    uint64_t cycles_done;
+    double t_arrive, t_start, t_done;   /* seconds since the server started */
+} sim_job_status;
+
+void sim_server_config_default(sim_server_config *cfg);
+int sim_server_create(const sim_server_config *cfg, sim_server **out);
+/* Queue a job; returns its id.  Errors: BADARG, ADMISSION (a single job larger
+ * than the cap). */
+int sim_submit(sim_server *s, const sim_job *job, uint64_t *job_id);
+/* Status of a job (never blocks).  A failed job returns SIM_ERR_STATE with
+ * the reason in sim_last_error(). */
+int sim_poll(sim_server *s, uint64_t job_id, sim_job_status *st);
+/* Block until the job is done or failed, at most timeout_ms (SIM_ERR_TIMEOUT). */
+int sim_server_wait(sim_server *s, uint64_t job_id, uint32_t timeout_ms);
+/* Per-instance final state digests of a done job (n_inst values). */
+int sim_job_digests(sim_server *s, uint64_t job_id, uint64_t *out);
+/* Totals: instance-cycles simulated, kernels launched, pool bytes in use. */
+int sim_server_stats(sim_server *s, uint64_t *instance_cycles, uint64_t *kernels, uint64_t *bytes_in_use);
+/* Device bytes a pool of `slots` instance slots of this netlist holds (the
+ * quantity admission compares with hbm_cap_bytes). */
+size_t sim_server_footprint(const sim_netlist *nl, uint32_t slots);
+/* Stops the worker after the steps in flight and frees every pool. */
+void sim_server_destroy(sim_server *s);
+
 const char *sim_last_error(void);
 
 #ifdef __cplusplus

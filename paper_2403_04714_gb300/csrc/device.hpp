@@ -36,6 +36,7 @@ struct DevState {
     uint64_t* mem;              // all memories, instance-minor
     uint64_t* rec[2];           // write records [n_wport][I][2]: (en<<63 | addr, data)
     const uint64_t* key;        // stimulus key per instance
+    const uint64_t* t_off;      // per instance: cycle at which its job started (pooled serving), or null
     const uint64_t* hold_val;   // [n_in][I]
     const uint8_t* hold_flag;   // [n_in][I]
     uint64_t* ring;             // per-cycle digests [cap][n_tracked]

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "../../include/sim.h"
 #include "device.hpp"
@@ -140,6 +141,7 @@ __device__ __forceinline__ uint64_t stimulus(const DevProg& P, const DevState& S
         uint64_t j = (uint64_t)k * S.I + inst;
         if (S.hold_flag[j]) return S.hold_val[j] & wmask(w);
     }
+    if (S.t_off) t -= S.t_off[inst];     // pooled slot: the job's own cycle count
     return mix64(key + (t * P.n_in + k + 1) * kGamma) & wmask(w);
 }
 
@@ -449,6 +451,46 @@ __global__ void k_commit(DevProg P, DevState S, uint64_t t_end, const uint64_t* 
 // Advance the device-resident cycle base of a replayed graph chunk.
 __global__ void k_advance(uint64_t* t0_dev, uint64_t n) { *t0_dev += n; }
 
+// Reset instances [lo, lo+n) of buffer `par` to the initial state: register
+// init values, memory images, memory digest terms and held inputs.  Used by
+// the server when a job takes over instance slots of a pool.
+__global__ void k_reset_slots(DevProg P, DevState S, uint32_t par, uint32_t lo, uint32_t n, const uint64_t* reg_init,
+                              const uint64_t* mem_image, const uint64_t* mem_word_off, uint64_t mem_words,
+                              const uint64_t* mem_init_dig, uint64_t rom_init_dig) {
+    const uint64_t gtid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, gth = (uint64_t)gridDim.x * blockDim.x;
+    // registers: one thread per (register, instance), or per (register, word) for packed 1-bit planes
+    const uint32_t w_lo = lo / S.pack, w_hi = (lo + n - 1) / S.pack;
+    for (uint64_t e = gtid; e < (uint64_t)P.n_reg * n; e += gth) {
+        uint32_t r = uint32_t(e / n), inst = lo + uint32_t(e % n);
+        uint32_t cls = P.reg_cls[r], idx = P.reg_idx[r];
+        if (cls == RC_W64) S.w64[par][(uint64_t)idx * S.I + inst] = reg_init[r];
+        else if (cls == RC_W32) S.w32[par][(uint64_t)idx * S.I + inst] = uint32_t(reg_init[r]);
+    }
+    for (uint64_t e = gtid; e < (uint64_t)P.n_reg * (w_hi - w_lo + 1); e += gth) {
+        uint32_t r = uint32_t(e / (w_hi - w_lo + 1)), wi = w_lo + uint32_t(e % (w_hi - w_lo + 1));
+        if (P.reg_cls[r] != RC_BIT) continue;
+        uint32_t b0 = wi * S.pack, mask = 0;
+        for (uint32_t b = 0; b < S.pack; b++)
+            if (b0 + b >= lo && b0 + b < lo + n) mask |= 1u << b;
+        uint32_t* word = S.bits[par] + (uint64_t)P.reg_idx[r] * S.bit_stride + wi;
+        *word = (*word & ~mask) | ((reg_init[r] & 1) ? mask : 0u);
+    }
+    for (uint64_t e = gtid; e < mem_words * n; e += gth) {
+        uint64_t wdx = e / n;
+        uint32_t inst = lo + uint32_t(e % n), m = 0;
+        while (m + 1 < P.n_mem && mem_word_off[m + 1] <= wdx) m++;
+        uint64_t a = wdx - mem_word_off[m];
+        S.mem[P.mem_base[m] + a * S.I + inst] = mem_image[wdx];
+    }
+    for (uint64_t e = gtid; e < (uint64_t)P.n_mem * n; e += gth) {
+        uint32_t m = uint32_t(e / n), inst = lo + uint32_t(e % n);
+        S.mem_dig[(uint64_t)m * S.I + inst] = mem_init_dig[m];
+    }
+    for (uint64_t e = gtid; e < n; e += gth) const_cast<uint64_t*>(S.rom_dig)[lo + e] = rom_init_dig;
+    for (uint64_t e = gtid; e < (uint64_t)P.n_in * n; e += gth)
+        const_cast<uint8_t*>(S.hold_flag)[(e / n) * S.I + lo + e % n] = 0;
+}
+
 // Full digest of buffer `par`: registers (part 0) and memory words (part 1),
 // each thread summing a chunk of items for one instance.
 __global__ void k_state_digest(DevProg P, DevState S, uint32_t par, const uint64_t* mem_word_off, uint64_t mem_words,
@@ -485,13 +527,20 @@ static void* cycles_fn(int mode, bool digest) {
     return digest ? kfun<SIM_MODE_LANE_OP, true>() : kfun<SIM_MODE_LANE_OP, false>();
 }
 
+// The dynamic shared-memory limit is a per-function attribute shared by every
+// batch in the process (and every thread): it is only ever raised, so a
+// smaller batch never lowers it under a larger one.
 cudaError_t prepare_cycles_kernel(int mode, size_t smem) {
-    cudaError_t e = cudaSuccess;
+    static std::mutex mu;
+    static size_t set_to[3][2] = {};
+    std::lock_guard<std::mutex> g(mu);
     for (int d = 0; d < 2; d++) {
-        e = cudaFuncSetAttribute(cycles_fn(mode, d), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (smem <= set_to[mode][d]) continue;
+        cudaError_t e = cudaFuncSetAttribute(cycles_fn(mode, d), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
+        set_to[mode][d] = smem;
     }
-    return e;
+    return cudaSuccess;
 }
 
 cudaError_t occupancy_cycles(int mode, int threads, size_t smem, int* blocks_per_sm) {
@@ -512,6 +561,14 @@ cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int
 cudaError_t launch_commit(int grid, cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t_end,
                           const uint64_t* t0_dev) {
     k_commit<<<grid, 256, 0, st>>>(P, S, t_end, t0_dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reset_slots(cudaStream_t st, const DevProg& P, const DevState& S, uint32_t par, uint32_t lo, uint32_t n,
+                               const uint64_t* reg_init, const uint64_t* mem_image, const uint64_t* mem_word_off,
+                               uint64_t mem_words, const uint64_t* mem_init_dig, uint64_t rom_init_dig) {
+    k_reset_slots<<<256, 256, 0, st>>>(P, S, par, lo, n, reg_init, mem_image, mem_word_off, mem_words, mem_init_dig,
+                                       rom_init_dig);
     return cudaGetLastError();
 }
 

@@ -107,8 +107,11 @@ struct sim_netlist {
     std::vector<uint64_t> mem_word_off;   // per-instance word offset of each memory (+ total)
 };
 
+namespace rtl { struct PoolExtra; void pool_extra_free(PoolExtra*); }
+
 struct sim_batch {
     sim_netlist* nl = nullptr;
+    rtl::PoolExtra* pool = nullptr;        // set for server pools
     cudaStream_t stream = nullptr;
     int mode = SIM_MODE_LANE_OP;
     int kernel = SIM_KERNEL_PERSISTENT;
@@ -139,6 +142,7 @@ struct sim_batch {
     DevState graph_state{};               // state descriptor captured in the graph
     bool own_stream = false;
     ~sim_batch() {
+        if (pool) rtl::pool_extra_free(pool);
         if (graph) cudaGraphExecDestroy(graph);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
@@ -1080,5 +1084,96 @@ int batch_views(sim_batch* b, DevProg* P, DevState* S, const uint64_t** mem_word
 }
 
 int batch_sync(sim_batch* b) { return sim_sync(b); }
+
+}  // namespace rtl
+
+// ---- instance pools for the server (pool.hpp) ---------------------------------
+#include "pool.hpp"
+
+namespace rtl {
+cudaError_t launch_reset_slots(cudaStream_t st, const DevProg& P, const DevState& S, uint32_t par, uint32_t lo, uint32_t n,
+                               const uint64_t* reg_init, const uint64_t* mem_image, const uint64_t* mem_word_off,
+                               uint64_t mem_words, const uint64_t* mem_init_dig, uint64_t rom_init_dig);
+
+struct PoolExtra {
+    DBuf t_off, reg_init, mem_image, mem_init_dig;
+    uint64_t rom_init_dig = 0;
+};
+
+size_t pool_footprint(const sim_netlist* h, uint32_t capacity) {
+    const Netlist& nl = h->nl;
+    const RegLayout& L = h->layout;
+    uint64_t I = (uint64_t(capacity) + 31) / 32 * 32;
+    uint64_t per = 2 * (uint64_t(L.count[RC_W64]) * 8 + uint64_t(L.count[RC_W32]) * 4 + (L.count[RC_BIT] + 7) / 8);
+    per += h->mem_word_off.back() * 8 + nl.wports.size() * 32 + nl.in_w.size() * 9 + nl.mem_lg.size() * 8 + 40;
+    uint64_t prog = (h->low.s_ins.size() + h->low.b_ins.size()) * 16 + h->low.c_words.size() * 4;
+    return size_t(per * I + prog + 2 * h->mem_word_off.back() * 8);
+}
+
+int pool_create(sim_netlist* nl, uint32_t capacity, sim_batch** out) {
+    if (!nl || !out || capacity == 0) return set_err(SIM_ERR_BADARG, "bad argument");
+    sim_config saved = nl->cfg;
+    nl->cfg.mode = SIM_MODE_LANE_INST;
+    nl->cfg.kernel = SIM_KERNEL_PER_CYCLE;
+    nl->cfg.digest_capacity = 0;
+    int rc = sim_create_instances(nl, capacity, 0, nullptr, out);
+    nl->cfg = saved;
+    if (rc) return rc;
+    sim_batch* b = *out;
+    std::unique_ptr<PoolExtra> x(new PoolExtra());
+    const Netlist& N = nl->nl;
+    std::vector<uint64_t> zeros(b->I, 0), image(nl->mem_word_off.back(), 0), mdig(N.mem_lg.size(), 0);
+    for (size_t m = 0; m < N.mem_lg.size(); m++) {
+        for (auto& [a, v] : N.mem_init[m]) image[nl->mem_word_off[m] + a] = v;
+        uint64_t d = 0;
+        for (uint64_t a = 0; a < (1ULL << N.mem_lg[m]); a++)
+            d += host_mix64(mem_hash(m, a) ^ image[nl->mem_word_off[m] + a]);
+        mdig[m] = d;
+        if (N.mem_ports[m].empty()) x->rom_init_dig += d;
+    }
+    if ((rc = upload(x->t_off, zeros, b->stream)) || (rc = upload(x->reg_init, N.reg_init, b->stream)) ||
+        (rc = upload(x->mem_image, image, b->stream)) || (rc = upload(x->mem_init_dig, mdig, b->stream))) {
+        sim_batch_destroy(b);
+        *out = nullptr;
+        return rc;
+    }
+    b->S.t_off = x->t_off.as<uint64_t>();
+    b->pool = x.release();
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    return SIM_OK;
+}
+
+int pool_admit(sim_batch* b, uint32_t lo, uint32_t n, uint64_t seed) {
+    if (!b || !b->pool || n == 0 || uint64_t(lo) + n > b->n_inst) return set_err(SIM_ERR_BADARG, "bad slot range");
+    PoolExtra* x = b->pool;
+    std::vector<uint64_t> keys(n), offs(n, b->cycle);
+    for (uint32_t j = 0; j < n; j++) keys[j] = host_mix64(seed + (uint64_t(j) + 1) * kGamma);
+    CUDA_TRY(cudaMemcpyAsync(b->key.as<uint64_t>() + lo, keys.data(), n * 8, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaMemcpyAsync(x->t_off.as<uint64_t>() + lo, offs.data(), n * 8, cudaMemcpyHostToDevice, b->stream));
+    for (size_t k = 0; k < b->nl->nl.in_w.size(); k++)
+        std::fill(b->h_hold_flag.begin() + k * b->I + lo, b->h_hold_flag.begin() + k * b->I + lo + n, 0);
+    CUDA_TRY(launch_reset_slots(b->stream, b->P, b->S, uint32_t(b->cycle & 1), lo, n, x->reg_init.as<uint64_t>(),
+                                x->mem_image.as<uint64_t>(), b->mem_word_off.as<uint64_t>(), b->nl->mem_word_off.back(),
+                                x->mem_init_dig.as<uint64_t>(), x->rom_init_dig));
+    b->kernels_launched++;
+    CUDA_TRY(cudaStreamSynchronize(b->stream));    // the host vectors above go out of scope
+    return SIM_OK;
+}
+
+int pool_step(sim_batch* b, uint64_t n) { return sim_step(b, n); }
+
+void pool_extra_free(PoolExtra* x) { delete x; }
+
+int pool_digests(sim_batch* b, uint32_t lo, uint32_t n, uint64_t* out) {
+    if (!b || uint64_t(lo) + n > b->n_inst) return set_err(SIM_ERR_BADARG, "bad slot range");
+    std::vector<uint64_t> all(b->n_inst);
+    int rc = sim_state_digests(b, all.data());
+    if (rc) return rc;
+    std::copy(all.begin() + lo, all.begin() + lo + n, out);
+    return SIM_OK;
+}
+
+cudaStream_t pool_stream(sim_batch* b) { return b->stream; }
+uint64_t pool_cycle(sim_batch* b) { return b->cycle; }
 
 }  // namespace rtl

@@ -561,11 +561,17 @@ def gen_mesh(seed=1002, mesh=4, ops_per_block=120_000, regs_per_block=8_000, dep
     return nl
 
 
+def gen_mesh_small(seed=1003) -> Netlist:
+    """A 2x2 mesh of 30k-op blocks: the mesh shape at served-job scale."""
+    return gen_mesh(seed, mesh=2, ops_per_block=30_000, regs_per_block=2_000, depth=40, inputs_per_block=8)
+
+
 CONFIGS = {
     "tiny": dict(gen=gen_tiny, seed=1000, n_inst=1, cycles=10_000, stim_seed=42),
     "mid": dict(gen=gen_mid, seed=1001, n_inst=1, cycles=100_000, stim_seed=42),
     "mesh": dict(gen=gen_mesh, seed=1002, n_inst=1, cycles=1_000_000, stim_seed=42),
     "batched": dict(gen=gen_mid, seed=1001, n_inst=4096, cycles=100_000, stim_seed=42),
+    "mesh_small": dict(gen=gen_mesh_small, seed=1003, n_inst=1, cycles=10_000, stim_seed=42),
 }
 
 
@@ -581,3 +587,24 @@ def cached_netlist(name: str, cache_dir: str | None = None, **overrides) -> str:
     if not os.path.exists(path):
         cfg["gen"](cfg["seed"]).save(path)
     return path
+
+
+def served_trace(n_jobs=40, rate=200.0, seed=7, inst_max=1024, cycles_lo=1e2, cycles_hi=3e3,
+                 shapes=(("tiny", 0.6), ("mid", 0.3), ("mesh_small", 0.1))):
+    """Seeded job trace: Poisson arrivals, shape by weight, instances and
+    cycle budgets log-uniform.  Returns (arrival_s, shape, pool_index, n_inst, n_cycles, seed)."""
+    import math
+    rng = random.Random(seed)
+    t, out = 0.0, []
+    for j in range(n_jobs):
+        t += rng.expovariate(rate)
+        x, acc, shape = rng.random(), 0.0, shapes[-1][0]
+        for name, wgt in shapes:
+            acc += wgt
+            if x < acc:
+                shape = name
+                break
+        n_inst = max(1, min(inst_max, int(round(math.exp(rng.uniform(0, math.log(inst_max)))))))
+        cyc = int(round(math.exp(rng.uniform(math.log(cycles_lo), math.log(cycles_hi)))))
+        out.append((t, shape, rng.randrange(1 << 30), n_inst, cyc, 1000 + j))
+    return out

@@ -88,7 +88,32 @@ EXPORTS = {
     "sim_last_error": (C.c_char_p, []),
     "sim_netlist_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "sim_state_digests_noalloc": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sim_server_config_default": (None, [C.c_void_p]),
+    "sim_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sim_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sim_poll": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
+    "sim_server_wait": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint32]),
+    "sim_job_digests": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p]),
+    "sim_server_stats": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sim_server_destroy": (None, [C.c_void_p]),
+    "sim_server_footprint": (C.c_size_t, [C.c_void_p, C.c_uint32]),
 }
+
+JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
+
+
+class sim_server_config(C.Structure):
+    _fields_ = [("struct_size", C.c_uint32), ("pool_slots", C.c_uint32), ("hbm_cap_bytes", C.c_uint64),
+                ("chunk_cycles", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+
+
+class sim_job(C.Structure):
+    _fields_ = [("netlist", C.c_void_p), ("n_inst", C.c_uint32), ("seed", C.c_uint64), ("n_cycles", C.c_uint64)]
+
+
+class sim_job_status(C.Structure):
+    _fields_ = [("state", C.c_int32), ("n_inst", C.c_uint32), ("cycles_done", C.c_uint64),
+                ("t_arrive", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
 
 TABLES = {"s_ins": (0, None), "s_off": (1, np.uint32), "s_len": (2, np.uint32), "b_ins": (3, None),
           "b_off": (4, np.uint32), "b_len": (5, np.uint32), "fiber_proc": (6, np.int32),
@@ -297,3 +322,55 @@ class Batch:
 
     def debug_skip_arrival(self, timeout_ms: int):
         _check(lib().sim_debug_skip_arrival(self._h, timeout_ms))
+
+
+class Server:
+    """sim_server_create: continuous-batching job server (one pool per netlist)."""
+
+    def __init__(self, **cfg):
+        c = sim_server_config()
+        lib().sim_server_config_default(C.byref(c))
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        h = C.c_void_p()
+        _check(lib().sim_server_create(C.byref(c), C.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, netlist: Netlist, n_inst: int, seed: int, n_cycles: int) -> int:
+        j = sim_job(netlist._h.value, n_inst, seed, n_cycles)
+        jid = C.c_uint64()
+        _check(lib().sim_submit(self._h, C.byref(j), C.byref(jid)))
+        self._keep[jid.value] = netlist          # the netlist must outlive its job
+        return jid.value
+
+    def poll(self, job_id: int) -> dict:
+        st = sim_job_status()
+        _check(lib().sim_poll(self._h, job_id, C.byref(st)))
+        return {"state": JOB_STATES[st.state], "n_inst": st.n_inst, "cycles_done": st.cycles_done,
+                "t_arrive": st.t_arrive, "t_start": st.t_start, "t_done": st.t_done}
+
+    def wait(self, job_id: int, timeout_ms: int = 600_000):
+        _check(lib().sim_server_wait(self._h, job_id, timeout_ms))
+
+    def digests(self, job_id: int, n_inst: int) -> np.ndarray:
+        out = np.zeros(n_inst, dtype=np.uint64)
+        _check(lib().sim_job_digests(self._h, job_id, out.ctypes.data))
+        return out
+
+    @staticmethod
+    def footprint(netlist: Netlist, slots: int) -> int:
+        return lib().sim_server_footprint(netlist._h, slots)
+
+    def stats(self) -> dict:
+        a, b, c = C.c_uint64(), C.c_uint64(), C.c_uint64()
+        _check(lib().sim_server_stats(self._h, C.byref(a), C.byref(b), C.byref(c)))
+        return {"instance_cycles": a.value, "kernels": b.value, "bytes_in_use": c.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sim_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

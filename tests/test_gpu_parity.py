@@ -238,3 +238,52 @@ def test_barrier_timeout_is_reported(tiny_text):
     with pytest.raises(sim.SimError) as e:
         b.sync()
     assert e.value.name == "SIM_ERR_TIMEOUT"
+
+
+def test_mesh_single_instance():
+    # the 2M-op 4x4 mesh: every cycle of a prefix against the oracle, then the
+    # closed-form registers after a longer run
+    from test_oracle_closed_forms import fib_pair, mac_closed
+    path = netgen.cached_netlist("mesh")
+    text = open(path).read()
+    n = 200
+    nl = sim.Netlist(text, mode="lane_op", digest_capacity=n + 1)
+    b = sim.Batch(nl, 1, seed=42)
+    b.step(n)
+    b.sync()
+    want, ref = oracle_digests(path, 42, 0, n, is_path=True)
+    assert first_mismatch(b.digests(0, 0, n + 1), want) is None
+    assert np.array_equal(b.regs(0), ref.regs())
+    names = netgen.parse_names(text)
+    b.step(4800)
+    b.sync()
+    assert b.peek_reg(0, names["chk_counter16"]) == 5000
+    assert b.peek_reg(0, names["chk_fib_b"]) == fib_pair(5000)[1]
+    assert b.peek_reg(0, names["chk_mac"]) == mac_closed(5000)
+
+
+def test_mesh_batched_sampled():
+    path = netgen.cached_netlist("mesh")
+    text = open(path).read()
+    n, insts = 40, [0, 63, 17]
+    nl = sim.Netlist(text, mode="lane_inst", target_processes=2432, digest_capacity=n + 1)
+    b = sim.Batch(nl, 64, seed=3, track=insts)
+    b.step(n)
+    b.sync()
+    wants = [oracle_digests(path, 3, i, n, is_path=True)[0] for i in insts]
+    for i, want in zip(insts, wants):
+        assert first_mismatch(b.digests(i, 0, n + 1), want) is None, i
+
+
+def test_batches_with_different_shared_memory_coexist(tiny_text, mid_text):
+    # the kernel's shared-memory limit is process-wide: creating a batch that
+    # needs less must not break a batch that needs more
+    big = sim.Batch(sim.Netlist(mid_text, mode="lane_inst", target_processes=256), 64, seed=1)
+    small = sim.Batch(sim.Netlist(tiny_text, mode="lane_inst"), 32, seed=1)
+    big.step(3)
+    small.step(3)
+    big.sync()
+    small.sync()
+    ref = oracle.Sim(oracle.Net(text=mid_text), 1, 0)
+    ref.run(3)
+    assert big.state_digests()[0] == ref.digest()
