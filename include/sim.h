@@ -70,6 +70,21 @@ enum { SIM_MODE_AUTO = 0, SIM_MODE_LANE_OP = 1, SIM_MODE_LANE_INST = 2 };
  *                graph and replayed. */
 enum { SIM_KERNEL_PERSISTENT = 0, SIM_KERNEL_PER_CYCLE = 1, SIM_KERNEL_PER_CYCLE_GRAPH = 2 };
 
+/* How processes are lowered.
+ *   BYTECODE:  a compact 16-byte instruction stream run by one interpreter
+ *              kernel (no compile step).
+ *   GENERATED: straight-line CUDA per process (values in registers),
+ *              compiled for sm_103a at the first sim_create_instances of
+ *              each lane mapping with NVRTC and nvJitLink; linked modules are
+ *              cached under $RTLSIM_GENCACHE when that is set. */
+enum { SIM_LOWER_BYTECODE = 0, SIM_LOWER_GENERATED = 1 };
+
+/* Task order.  GROUP_MAJOR: neighbouring warps run different processes of
+ * the same instances (their state stays in L2).  PROCESS_MAJOR: neighbouring
+ * warps run the same process for different instance groups (its code and
+ * program stay hot in the SM).  AUTO: PROCESS_MAJOR for LANE_INST. */
+enum { SIM_ORDER_AUTO = 0, SIM_ORDER_GROUP_MAJOR = 1, SIM_ORDER_PROCESS_MAJOR = 2 };
+
 typedef struct sim_config {
     uint32_t struct_size;       /* sizeof(sim_config) */
     int32_t mode;               /* SIM_MODE_* */
@@ -82,7 +97,9 @@ typedef struct sim_config {
     uint64_t big_array_bytes;   /* SLB stage-1 threshold (paper default 128 KiB) */
     uint32_t disable_stage3;    /* testing: skip the conservative merge */
     uint32_t seed_partition;    /* testing: 0 = SLB; else a random partition with this seed */
-    uint32_t reserved[8];
+    uint32_t lowering;          /* SIM_LOWER_BYTECODE or SIM_LOWER_GENERATED */
+    uint32_t task_order;        /* SIM_ORDER_*: how (process, instance group) tasks map to warps */
+    uint32_t reserved[6];
 } sim_config;
 
 typedef struct sim_netlist_info {
@@ -113,6 +130,13 @@ void sim_config_default(sim_config *cfg);
 int sim_load_netlist(const void *text, size_t len, const sim_config *cfg, sim_netlist **out);
 int sim_netlist_get_info(const sim_netlist *nl, sim_netlist_info *out);
 void sim_netlist_destroy(sim_netlist *nl);
+
+/* Generate and compile (NVRTC + nvJitLink, no GPU needed) the generated-CUDA
+ * lowering of one lane mapping ahead of sim_create_instances, e.g. to fill
+ * the $RTLSIM_GENCACHE cache.  *seconds: compile (or cache read) time;
+ * *cached: 1 if the linked module came from the cache.  Errors: BADARG, CUDA
+ * (compile or link failure, message in sim_last_error). */
+int sim_netlist_compile_generated(sim_netlist *nl, int32_t mode, double *seconds, int32_t *cached);
 
 /* Introspection of the compiled program (tests and tools).  With out == NULL
  * *bytes receives the table size; otherwise min(*bytes, size) bytes are

@@ -16,7 +16,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgb300sim.so")
-SOURCES = ["kernels.cu", "runtime.cpp", "compiler.cpp", "noalloc.cu", "server.cpp"]
+SOURCES = ["kernels.cu", "runtime.cpp", "compiler.cpp", "noalloc.cu", "server.cpp", "codegen.cpp", "jit.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -54,10 +54,30 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        objs = list(ex.map(compile_one, SOURCES))
+    # the device runtime header and the ABI header are compiled into the
+    # library as strings: NVRTC compiles them with the generated code
+    emb = os.path.join(out_dir, "embedded_headers.cpp")
+    with open(emb + ".tmp", "w") as f:
+        f.write("namespace rtl {\n")
+        for sym, name in (("kEmbeddedAbiHeader", "abi_device.h"), ("kEmbeddedRtHeader", "sim_rt.cuh")):
+            text = open(os.path.join(CSRC, name)).read()
+            assert ")RTLSIM_EMBED\"" not in text
+            f.write(f"extern const char* const {sym};\nconst char* const {sym} = R\"RTLSIM_EMBED({text})RTLSIM_EMBED\";\n")
+        f.write("}  // namespace rtl\n")
+    os.replace(emb + ".tmp", emb)
+
+    def compile_emb():
+        obj = emb + ".o"
+        subprocess.run([cc, *common, "-c", emb, "-o", obj], check=True, capture_output=True)
+        return obj
+
+    with cf.ThreadPoolExecutor(len(SOURCES) + 1) as ex:
+        futs = [ex.submit(compile_one, s) for s in SOURCES] + [ex.submit(compile_emb)]
+        objs = [f.result() for f in futs]
     tmp = f"{LIB}.tmp{os.getpid()}"
-    cmd = [cc, "-shared", *ARCH, *objs, "-o", tmp, "-lcudart"]
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    cmd = [cc, "-shared", *ARCH, *objs, "-o", tmp, "-lcudart", "-lnvrtc", "-lnvJitLink",
+           "-Xlinker", f"-rpath,{cuda_lib}"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -14,6 +14,8 @@
 #include <string>
 #include <vector>
 
+#include "abi_device.h"
+
 namespace rtl {
 
 enum Op : uint8_t {
@@ -48,25 +50,7 @@ struct Netlist {
 // Parse and check.  Returns 0 or a negative SIM_ERR_* code with a message.
 int parse_netlist(const char* text, size_t len, Netlist& out, std::string& err);
 
-// Register storage classes (instance-minor planes on the device).
-enum RegClass : uint8_t { RC_BIT = 0, RC_W32 = 1, RC_W64 = 2 };
 inline RegClass reg_class(int w) { return w == 1 ? RC_BIT : (w <= 32 ? RC_W32 : RC_W64); }
-
-// ------------------------------------------------------------------------
-// Device bytecode.  16 bytes per instruction.
-// ------------------------------------------------------------------------
-enum DOp : uint8_t {
-    D_NOP = 0, D_LDR, D_LDI, D_CONST, D_MEMRD,
-    D_ADD, D_SUB, D_MUL, D_AND, D_OR, D_XOR, D_SHL, D_SHR, D_EQ, D_LT,
-    D_MUX, D_SLICE, D_CONCAT,
-    D_STR, D_WREC, D_COMMIT, D_COUNT
-};
-
-struct DIns {
-    uint8_t op, w;
-    uint16_t dst, a, b, c, x;
-    uint32_t imm;
-};
 static_assert(sizeof(DIns) == 16, "DIns is 16 bytes");
 
 struct PartitionConfig {

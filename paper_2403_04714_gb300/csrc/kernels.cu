@@ -25,69 +25,11 @@
 
 #include "../../include/sim.h"
 #include "device.hpp"
+#include "sim_rt.cuh"
 
 namespace rtl {
 
-constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
-
-__device__ __forceinline__ uint64_t mix64(uint64_t z) {
-    // SplitMix64 output function (Steele, Lea, Flood 2014)
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    return z ^ (z >> 31);
-}
-
-__device__ __forceinline__ uint64_t wmask(uint32_t w) { return ~0ULL >> (64 - w); }   // w in 1..64
-
-__device__ __forceinline__ uint64_t globaltimer_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *(volatile const int32_t*)p; }
-
 __device__ __forceinline__ uint4 ld_ins(const DIns* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
-
-// Grid-wide barrier: arrival counter plus generation word.  Every wait is
-// bounded: past `timeout_ns`, or once another CTA has recorded an error, the
-// CTA records SIM_ERR_TIMEOUT (first error wins) and returns false.
-__device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeout_ns, int32_t* err, bool skip) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        __threadfence();
-        if (!skip) {
-            uint32_t arrived = atomicAdd(&bar[0], 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(&bar[0], 0u);
-                __threadfence();
-                atomicExch(&bar[1], gen + 1);
-            }
-        }
-        uint64_t start = globaltimer_ns();
-        while (ld_acquire(&bar[1]) == gen) {
-            if (ld_volatile(err) != 0) { ok = 0; break; }
-            if (globaltimer_ns() - start > timeout_ns) {
-                atomicCAS(err, 0, SIM_ERR_TIMEOUT);
-                ok = 0;
-                break;
-            }
-        }
-        gen++;
-        __threadfence();
-        s_ok = ok;
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
 
 // ---------------------------------------------------------------------------
 // Instruction semantics (shared by both lane mappings)
@@ -126,76 +68,6 @@ __device__ __forceinline__ uint64_t alu(uint32_t op, uint64_t a, uint64_t b, uin
     case D_CONCAT: return (a << x) | b;    // width(b) < 64 (checked at load)
     default: return 0;
     }
-}
-
-__device__ __forceinline__ uint64_t load_reg(const DevState& S, uint32_t par, uint32_t cls, uint32_t idx, uint32_t inst) {
-    if (cls == RC_W64) return S.w64[par][(uint64_t)idx * S.I + inst];
-    if (cls == RC_W32) return S.w32[par][(uint64_t)idx * S.I + inst];
-    uint32_t word = S.bits[par][(uint64_t)idx * S.bit_stride + inst / S.pack];
-    return (word >> (inst % S.pack)) & 1u;
-}
-
-__device__ __forceinline__ uint64_t stimulus(const DevProg& P, const DevState& S, uint64_t key, uint32_t k, uint32_t inst,
-                                             uint64_t t, uint32_t w) {
-    if (S.any_hold) {
-        uint64_t j = (uint64_t)k * S.I + inst;
-        if (S.hold_flag[j]) return S.hold_val[j] & wmask(w);
-    }
-    if (S.t_off) t -= S.t_off[inst];     // pooled slot: the job's own cycle count
-    return mix64(key + (t * P.n_in + k + 1) * kGamma) & wmask(w);
-}
-
-__device__ __forceinline__ uint64_t mem_hash(uint32_t m, uint64_t a) {
-    return ((1ULL << 40) + ((uint64_t)m << 24) + a) * kGamma + 1ULL;
-}
-
-// Read memory m at addr for inst as of the clock edge: the array plus the
-// pending write records of the previous cycle (highest port wins).
-__device__ __forceinline__ uint64_t mem_read(const DevProg& P, const DevState& S, uint32_t m, uint64_t addr, uint32_t inst,
-                                             uint32_t prev, bool pending) {
-    uint64_t v = S.mem[P.mem_base[m] + addr * S.I + inst];
-    if (pending) {
-        for (uint32_t j = P.mport_off[m]; j < P.mport_off[m + 1]; j++) {
-            const uint64_t* r = S.rec[prev] + ((uint64_t)P.mport_id[j] * S.I + inst) * 2;
-            uint64_t ea = r[0];
-            if ((ea >> 63) && (ea & ~(1ULL << 63)) == addr) v = r[1];
-        }
-    }
-    return v;
-}
-
-// Apply the previous cycle's write records of memory m for one instance
-// (ascending port order) and return the change of the memory digest.
-__device__ __forceinline__ uint64_t mem_commit(const DevProg& P, const DevState& S, uint32_t m, uint32_t inst, uint32_t prev,
-                                               bool digest) {
-    uint64_t delta = 0;
-    for (uint32_t j = P.mport_off[m]; j < P.mport_off[m + 1]; j++) {
-        const uint64_t* r = S.rec[prev] + ((uint64_t)P.mport_id[j] * S.I + inst) * 2;
-        uint64_t ea = r[0];
-        if (ea >> 63) {
-            uint64_t addr = ea & ~(1ULL << 63);
-            uint64_t* cell = S.mem + P.mem_base[m] + addr * S.I + inst;
-            uint64_t old = *cell, nv = r[1];
-            *cell = nv;
-            if (digest) delta += mix64(mem_hash(m, addr) ^ nv) - mix64(mem_hash(m, addr) ^ old);
-        }
-    }
-    return delta;
-}
-
-__device__ __forceinline__ void ring_add(const DevState& S, uint64_t t, int32_t col, uint64_t v) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(S.ring + (t % S.ring_cap) * S.n_tracked + col),
-              (unsigned long long)v);
-}
-
-// Memory part of the digest at cycle t (records of t-1 just applied).
-__device__ __forceinline__ void mem_digest_update(const DevState& S, uint32_t m, uint32_t inst, uint64_t t, uint64_t delta) {
-    int32_t col = S.track[inst];
-    if (col < 0) return;
-    uint64_t* md = S.mem_dig + (uint64_t)m * S.I + inst;
-    uint64_t v = *md + delta;
-    *md = v;
-    ring_add(S, t, col, v);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,20 +254,6 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
 
-// Apply the last cycle's write records after the final barrier of a launch
-// (or in a launch of its own after per-cycle launches).
-__device__ void final_commit(const DevProg& P, const DevState& S, uint64_t t_end, uint64_t gtid, uint64_t gthreads) {
-    const uint32_t prev = uint32_t((t_end - 1) & 1);
-    const uint64_t total = (uint64_t)P.n_mem * S.I;
-    for (uint64_t e = gtid; e < total; e += gthreads) {
-        uint32_t m = uint32_t(e / S.I), inst = uint32_t(e % S.I);
-        if (P.mport_off[m] == P.mport_off[m + 1]) continue;
-        bool dig = S.ring_cap && S.track[inst] >= 0;
-        uint64_t delta = mem_commit(P, S, m, inst, prev, dig);
-        if (dig) mem_digest_update(S, m, inst, t_end, delta);
-    }
-}
-
 template <int MODE, bool DIGEST>
 __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
@@ -429,7 +287,11 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
             }
         } else {
             for (uint32_t task = warp; task < A.n_tasks; task += tw) {
-                uint32_t p = task % P.n_proc, g = task / P.n_proc;
+                // process-major order: neighbouring warps run the same process
+                // for different instance groups (its code and constants stay hot)
+                const uint32_t G = A.n_tasks / P.n_proc;
+                uint32_t p = A.proc_major ? task / G : task % P.n_proc;
+                uint32_t g = A.proc_major ? task % G : task / P.n_proc;
                 if (MODE == SIM_MODE_LANE_INST) task_lane_inst<DIGEST>(P, S, p, g, t, pending, sl, lane);
                 else task_lane_op<DIGEST>(P, S, p, g, t, pending, sl, lane);
             }

@@ -9,9 +9,11 @@
 #include <memory>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/sim.h"
+#include "codegen.hpp"
 #include "compiler.hpp"
 #include "device.hpp"
 
@@ -98,6 +100,15 @@ int upload(DBuf& b, const std::vector<T>& v, cudaStream_t st) {
 
 struct sim_netlist {
     sim_config cfg;
+    // generated-CUDA lowering, per lane mapping (built on first use)
+    std::mutex gen_mu;
+    std::vector<char> gen_cubin[3];
+    rtl::GenModule gen[3];
+    double gen_seconds[3] = {0, 0, 0};
+    bool gen_cached[3] = {false, false, false};
+    ~sim_netlist() {
+        for (auto& g : gen) rtl::jit_unload(g);
+    }
     Netlist nl;
     Partition part;
     Lowered low;
@@ -112,6 +123,9 @@ namespace rtl { struct PoolExtra; void pool_extra_free(PoolExtra*); }
 struct sim_batch {
     sim_netlist* nl = nullptr;
     rtl::PoolExtra* pool = nullptr;        // set for server pools
+    bool generated = false;                // processes run as generated CUDA
+    const void* gen_kernel[2] = {nullptr, nullptr};
+    DevState S_uploaded{};
     cudaStream_t stream = nullptr;
     int mode = SIM_MODE_LANE_OP;
     int kernel = SIM_KERNEL_PERSISTENT;
@@ -122,7 +136,7 @@ struct sim_batch {
         in_w, reg_cls, reg_idx, mem_word_off;
     // state
     DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, rom_dig, bar, err, t0_dev,
-        scratch;
+        scratch, P_dev, S_dev;
     DevProg P{};
     DevState S{};
     std::vector<uint8_t> h_hold_flag;     // host mirror
@@ -133,6 +147,7 @@ struct sim_batch {
     int threads = 256, warps = 8, grid = 0, max_grid = 0;
     size_t smem = 0;
     uint32_t slot_words = 0, prog_words = 0, n_tasks = 0;
+    uint32_t proc_major = 0;                // task order (see LaunchArgs)
     uint64_t kernels_launched = 0;
     int32_t skip_cta = -1;
     uint64_t timeout_ns = 2000000000ULL;
@@ -160,6 +175,10 @@ struct sim_batch {
         return SIM_OK;
     }
 };
+
+namespace {
+int ensure_compiled(sim_netlist* h, int mode);
+}
 
 extern "C" {
 
@@ -242,6 +261,15 @@ int sim_netlist_get_info(const sim_netlist* nl, sim_netlist_info* out) {
 
 void sim_netlist_destroy(sim_netlist* nl) { delete nl; }
 
+int sim_netlist_compile_generated(sim_netlist* nl, int32_t mode, double* seconds, int32_t* cached) {
+    if (!nl || (mode != SIM_MODE_LANE_OP && mode != SIM_MODE_LANE_INST)) return set_err(SIM_ERR_BADARG, "bad argument");
+    int rc = ensure_compiled(nl, mode);
+    if (rc) return rc;
+    if (seconds) *seconds = nl->gen_seconds[mode];
+    if (cached) *cached = nl->gen_cached[mode] ? 1 : 0;
+    return SIM_OK;
+}
+
 int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* bytes) {
     if (!nl || !bytes) return set_err(SIM_ERR_BADARG, "null argument");
     const Lowered& L = nl->low;
@@ -293,6 +321,96 @@ int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* b
 }  // extern "C"
 
 namespace {
+
+// Generate and compile (once per lane mapping) the netlist's CUDA lowering.
+int ensure_compiled(sim_netlist* h, int mode) {
+    std::lock_guard<std::mutex> g(h->gen_mu);
+    if (!h->gen_cubin[mode].empty()) return SIM_OK;
+    std::vector<rtl::GenUnit> units;
+    std::string err;
+    unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    int chunks = int(std::min<size_t>(std::max<size_t>(1, h->part.procs.size() / 16), size_t(hw) * 2));
+    int rc = rtl::gen_cuda(h->nl, h->part, mode, chunks, units, err);
+    if (rc) return set_err(rc, err);
+    if (const char* dump = getenv("RTLSIM_GEN_DUMP")) {     // developer aid: keep the generated sources
+        for (auto& u : units) {
+            FILE* f = fopen((std::string(dump) + "/" + u.name).c_str(), "w");
+            if (f) {
+                fwrite(u.source.data(), 1, u.source.size(), f);
+                fclose(f);
+            }
+        }
+    }
+    const char* dir = getenv("RTLSIM_GENCACHE");
+    std::string cache = dir ? dir : "";
+    if (!cache.empty()) {
+        std::string mk = "mkdir -p '" + cache + "'";
+        if (system(mk.c_str()) != 0) cache.clear();
+    }
+    bool cached = false;
+    double sec = 0;
+    rc = rtl::jit_compile(units, cache, h->gen_cubin[mode], &cached, &sec, err);
+    if (rc) return set_err(rc, err);
+    h->gen_seconds[mode] = sec;
+    h->gen_cached[mode] = cached;
+    return SIM_OK;
+}
+
+int ensure_loaded(sim_netlist* h, int mode) {
+    int rc = ensure_compiled(h, mode);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> g(h->gen_mu);
+    if (h->gen[mode].lib) return SIM_OK;
+    std::string err;
+    rc = rtl::jit_load(h->gen_cubin[mode], h->gen[mode], err);
+    if (rc) return set_err(rc, err);
+    return SIM_OK;
+}
+
+// Launch plan for generated code: no shared memory, occupancy from registers.
+int plan_launch_gen(sim_batch* b) {
+    const int sms = sm_count();
+    const uint32_t n_proc = uint32_t(b->nl->part.procs.size());
+    b->n_tasks = b->mode == SIM_MODE_LANE_INST ? n_proc * (b->I / 32) : n_proc * b->I;
+    b->slot_words = 0;
+    b->prog_words = 0;
+    b->smem = 0;
+    // generated kernels are compiled for at most 256 threads per CTA
+    int warps = std::min(8, b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8);
+    b->warps = warps;
+    b->threads = warps * 32;
+    int occ = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->gen_kernel[0], b->threads, 0));
+    int occ1 = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, b->gen_kernel[1], b->threads, 0));
+    occ = std::min(occ, occ1);
+    if (occ < 1) return set_err(SIM_ERR_CAPACITY, "generated kernel does not fit on an SM");
+    b->max_grid = occ * sms;
+    int need = int((b->n_tasks + warps - 1) / warps);
+    b->grid = std::max(1, std::min(need, b->max_grid));
+    return SIM_OK;
+}
+
+// Keep the device copy of the state view (read by generated code) current.
+int sync_state_view(sim_batch* b) {
+    if (!b->generated || memcmp(&b->S_uploaded, &b->S, sizeof(DevState)) == 0) return SIM_OK;
+    int rc = b->h2d(b->S_dev.p, &b->S, sizeof(DevState));
+    if (rc) return rc;
+    b->S_uploaded = b->S;
+    return SIM_OK;
+}
+
+cudaError_t launch_any(sim_batch* b, bool cooperative, int grid, const LaunchArgs& A) {
+    if (!b->generated)
+        return launch_cycles(b->mode, b->S.ring_cap > 0, cooperative, grid, b->threads, b->smem, b->stream, b->P, b->S, A);
+    const void* f = b->gen_kernel[b->S.ring_cap > 0 ? 1 : 0];
+    const DevProg* Pd = b->P_dev.as<DevProg>();
+    const DevState* Sd = b->S_dev.as<DevState>();
+    LaunchArgs a = A;
+    void* args[] = {&Pd, &Sd, &a};
+    if (cooperative) return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(b->threads), args, 0, b->stream);
+    return cudaLaunchKernel(f, dim3(grid), dim3(b->threads), args, 0, b->stream);
+}
 
 // Largest sum of compact-program sizes over the processes one warp owns
 // (process p belongs to warp p mod total_warps), in 32-bit words.
@@ -564,6 +682,7 @@ LaunchArgs base_args(sim_batch* b) {
     A.prog_words = b->prog_words;
     A.n_tasks = b->n_tasks;
     A.group = b->mode == SIM_MODE_LANE_INST ? 32 : 1;
+    A.proc_major = b->proc_major;
     return A;
 }
 
@@ -590,7 +709,9 @@ int step_persistent(sim_batch* b, uint64_t n) {
     A.skip_cta = b->skip_cta;
     b->skip_cta = -1;
     CUDA_TRY(cudaMemsetAsync(b->bar.p, 0, 8, b->stream));
-    CUDA_TRY(launch_cycles(b->mode, b->S.ring_cap > 0, true, b->grid, b->threads, b->smem, b->stream, b->P, b->S, A));
+    int rc = sync_state_view(b);
+    if (rc) return rc;
+    CUDA_TRY(launch_any(b, true, b->grid, A));
     b->kernels_launched++;
     return SIM_OK;
 }
@@ -603,6 +724,8 @@ int per_cycle_grid(sim_batch* b) {
 }
 
 int step_per_cycle(sim_batch* b, uint64_t n) {
+    int rc = sync_state_view(b);
+    if (rc) return rc;
     LaunchArgs A = base_args(b);
     A.n = 1;
     A.grid_sync = 0;
@@ -610,7 +733,7 @@ int step_per_cycle(sim_batch* b, uint64_t n) {
     for (uint64_t k = 0; k < n; k++) {
         A.t0 = b->cycle + k;
         A.pending_first = k > 0;
-        CUDA_TRY(launch_cycles(b->mode, b->S.ring_cap > 0, false, grid, b->threads, b->smem, b->stream, b->P, b->S, A));
+        CUDA_TRY(launch_any(b, false, grid, A));
     }
     CUDA_TRY(launch_commit(std::max(1, b->grid), b->stream, b->P, b->S, b->cycle + n, nullptr));
     b->kernels_launched += n + 1;
@@ -622,6 +745,8 @@ int step_per_cycle(sim_batch* b, uint64_t n) {
 // cycle base, so it can be replayed for any starting cycle.
 int step_graph(sim_batch* b, uint64_t n) {
     const uint32_t chunk = 64;
+    int src = sync_state_view(b);
+    if (src) return src;
     if (!b->graph || b->graph_chunk != chunk || memcmp(&b->graph_state, &b->S, sizeof(DevState)) != 0) {
         b->graph_state = b->S;
         if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -637,7 +762,7 @@ int step_graph(sim_batch* b, uint64_t n) {
         for (uint32_t k = 0; k < chunk && e == cudaSuccess; k++) {
             A.t0 = k;
             A.pending_first = k > 0;
-            e = launch_cycles(b->mode, b->S.ring_cap > 0, false, grid, b->threads, b->smem, b->stream, b->P, b->S, A);
+            e = launch_any(b, false, grid, A);
         }
         if (e == cudaSuccess) e = launch_commit(std::max(1, b->grid), b->stream, b->P, b->S, chunk, A.t0_dev);
         if (e == cudaSuccess) e = launch_advance(b->stream, b->t0_dev.as<uint64_t>(), chunk);
@@ -707,8 +832,22 @@ int sim_create_instances(sim_netlist* nl, uint32_t n_inst, uint64_t seed, void* 
         b->kernel = nl->cfg.kernel;
         b->I = b->mode == SIM_MODE_LANE_INST ? (n_inst + 31) / 32 * 32 : n_inst;
         b->timeout_ns = uint64_t(nl->cfg.timeout_ms ? nl->cfg.timeout_ms : 2000) * 1000000ULL;
+        // lane = instance: process-major task order unless the config asks otherwise
+        b->proc_major = nl->cfg.task_order == SIM_ORDER_PROCESS_MAJOR ||
+                        (nl->cfg.task_order == SIM_ORDER_AUTO && b->mode == SIM_MODE_LANE_INST);
         int rc;
-        if ((rc = upload_program(b.get())) || (rc = init_state(b.get())) || (rc = plan_launch(b.get()))) return rc;
+        if ((rc = upload_program(b.get())) || (rc = init_state(b.get()))) return rc;
+        if (nl->cfg.lowering == SIM_LOWER_GENERATED) {
+            if ((rc = ensure_loaded(nl, b->mode))) return rc;
+            b->generated = true;
+            b->gen_kernel[0] = reinterpret_cast<const void*>(nl->gen[b->mode].kernel[0]);
+            b->gen_kernel[1] = reinterpret_cast<const void*>(nl->gen[b->mode].kernel[1]);
+            if ((rc = b->P_dev.alloc(sizeof(DevProg))) || (rc = b->S_dev.alloc(sizeof(DevState))) ||
+                (rc = b->h2d(b->P_dev.p, &b->P, sizeof(DevProg))) || (rc = plan_launch_gen(b.get())))
+                return rc;
+        } else if ((rc = plan_launch(b.get()))) {
+            return rc;
+        }
         if ((rc = setup_tracking(b.get(), {0}))) return rc;
         *out = b.release();
         return SIM_OK;

@@ -1,0 +1,235 @@
+// sim_rt.cuh -- device runtime shared by the bytecode kernels (kernels.cu) and
+// the generated per-process code compiled at run time: stimulus, register
+// and memory access, write-record forwarding and commit, digests, and the
+// bounded grid barrier.  Compiled by nvcc into the library and passed to
+// NVRTC as an in-memory header.
+#pragma once
+#include "abi_device.h"
+
+#ifndef SIM_ERR_TIMEOUT
+#define SIM_ERR_TIMEOUT (-6)
+#endif
+
+namespace rtl {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ULL;
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    // SplitMix64 output function (Steele, Lea, Flood 2014)
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t wmask(uint32_t w) { return ~0ULL >> (64 - w); }   // w in 1..64
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *(volatile const int32_t*)p; }
+
+
+// Grid-wide barrier: arrival counter plus generation word.  Every wait is
+// bounded: past `timeout_ns`, or once another CTA has recorded an error, the
+// CTA records SIM_ERR_TIMEOUT (first error wins) and returns false.
+static __device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeout_ns, int32_t* err, bool skip) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        if (!skip) {
+            uint32_t arrived = atomicAdd(&bar[0], 1u);
+            if (arrived == gridDim.x - 1) {
+                atomicExch(&bar[0], 0u);
+                __threadfence();
+                atomicExch(&bar[1], gen + 1);
+            }
+        }
+        uint64_t start = globaltimer_ns();
+        while (ld_acquire(&bar[1]) == gen) {
+            if (ld_volatile(err) != 0) { ok = 0; break; }
+            if (globaltimer_ns() - start > timeout_ns) {
+                atomicCAS(err, 0, (int32_t)SIM_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        gen++;
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+__device__ __forceinline__ uint64_t load_reg(const DevState& S, uint32_t par, uint32_t cls, uint32_t idx, uint32_t inst) {
+    if (cls == RC_W64) return S.w64[par][(uint64_t)idx * S.I + inst];
+    if (cls == RC_W32) return S.w32[par][(uint64_t)idx * S.I + inst];
+    uint32_t word = S.bits[par][(uint64_t)idx * S.bit_stride + inst / S.pack];
+    return (word >> (inst % S.pack)) & 1u;
+}
+
+__device__ __forceinline__ uint64_t stimulus(const DevProg& P, const DevState& S, uint64_t key, uint32_t k, uint32_t inst,
+                                             uint64_t t, uint32_t w) {
+    if (S.any_hold) {
+        uint64_t j = (uint64_t)k * S.I + inst;
+        if (S.hold_flag[j]) return S.hold_val[j] & wmask(w);
+    }
+    if (S.t_off) t -= S.t_off[inst];     // pooled slot: the job's own cycle count
+    return mix64(key + (t * P.n_in + k + 1) * kGamma) & wmask(w);
+}
+
+__device__ __forceinline__ uint64_t mem_hash(uint32_t m, uint64_t a) {
+    return ((1ULL << 40) + ((uint64_t)m << 24) + a) * kGamma + 1ULL;
+}
+
+// Read memory m at addr for inst as of the clock edge: the array plus the
+// pending write records of the previous cycle (highest port wins).
+__device__ __forceinline__ uint64_t mem_read(const DevProg& P, const DevState& S, uint32_t m, uint64_t addr, uint32_t inst,
+                                             uint32_t prev, bool pending) {
+    uint64_t v = S.mem[P.mem_base[m] + addr * S.I + inst];
+    if (pending) {
+        for (uint32_t j = P.mport_off[m]; j < P.mport_off[m + 1]; j++) {
+            const uint64_t* r = S.rec[prev] + ((uint64_t)P.mport_id[j] * S.I + inst) * 2;
+            uint64_t ea = r[0];
+            if ((ea >> 63) && (ea & ~(1ULL << 63)) == addr) v = r[1];
+        }
+    }
+    return v;
+}
+
+// Apply the previous cycle's write records of memory m for one instance
+// (ascending port order) and return the change of the memory digest.
+__device__ __forceinline__ uint64_t mem_commit(const DevProg& P, const DevState& S, uint32_t m, uint32_t inst, uint32_t prev,
+                                               bool digest) {
+    uint64_t delta = 0;
+    for (uint32_t j = P.mport_off[m]; j < P.mport_off[m + 1]; j++) {
+        const uint64_t* r = S.rec[prev] + ((uint64_t)P.mport_id[j] * S.I + inst) * 2;
+        uint64_t ea = r[0];
+        if (ea >> 63) {
+            uint64_t addr = ea & ~(1ULL << 63);
+            uint64_t* cell = S.mem + P.mem_base[m] + addr * S.I + inst;
+            uint64_t old = *cell, nv = r[1];
+            *cell = nv;
+            if (digest) delta += mix64(mem_hash(m, addr) ^ nv) - mix64(mem_hash(m, addr) ^ old);
+        }
+    }
+    return delta;
+}
+
+__device__ __forceinline__ void ring_add(const DevState& S, uint64_t t, int32_t col, uint64_t v) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(S.ring + (t % S.ring_cap) * S.n_tracked + col),
+              (unsigned long long)v);
+}
+
+// Memory part of the digest at cycle t (records of t-1 just applied).
+__device__ __forceinline__ void mem_digest_update(const DevState& S, uint32_t m, uint32_t inst, uint64_t t, uint64_t delta) {
+    int32_t col = S.track[inst];
+    if (col < 0) return;
+    uint64_t* md = S.mem_dig + (uint64_t)m * S.I + inst;
+    uint64_t v = *md + delta;
+    *md = v;
+    ring_add(S, t, col, v);
+}
+
+// Apply the last cycle's write records after the final barrier of a launch
+// (or in a launch of its own after per-cycle launches).
+static __device__ void final_commit(const DevProg& P, const DevState& S, uint64_t t_end, uint64_t gtid,
+                                    uint64_t gthreads) {
+    const uint32_t prev = uint32_t((t_end - 1) & 1);
+    const uint64_t total = (uint64_t)P.n_mem * S.I;
+    for (uint64_t e = gtid; e < total; e += gthreads) {
+        uint32_t m = uint32_t(e / S.I), inst = uint32_t(e % S.I);
+        if (P.mport_off[m] == P.mport_off[m + 1]) continue;
+        bool dig = S.ring_cap && S.track[inst] >= 0;
+        uint64_t delta = mem_commit(P, S, m, inst, prev, dig);
+        if (dig) mem_digest_update(S, m, inst, t_end, delta);
+    }
+}
+
+}  // namespace rtl
+
+// ---------------------------------------------------------------------------
+// Kernels for generated code (compiled at run time with the generated units).
+// The per-process functions rtl_p<k> and the dispatcher come from codegen.cpp.
+// ---------------------------------------------------------------------------
+#ifdef RTLSIM_GENERATED
+extern "C" __device__ void rtl_dispatch(uint32_t p, const rtl::DevProg* __restrict__ P,
+                                        const rtl::DevState* __restrict__ S, uint32_t g, uint64_t t, bool pending,
+                                        uint32_t lane, uint64_t* __restrict__ dacc, int32_t col);
+
+namespace rtl {
+
+// Same cycle loop as the bytecode kernel.  LANE_INST (mode 2): every lane runs
+// its instance through the process function.  LANE_OP (mode 1): lane 0 runs
+// the process for one instance.
+template <int MODE, bool DIGEST>
+__device__ __forceinline__ void gen_cycles(const DevProg* __restrict__ Pg, const DevState* __restrict__ Sg,
+                                           const LaunchArgs& A) {
+    const DevProg& P = *Pg;
+    const DevState& S = *Sg;
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t warp = blockIdx.x * A.warps_per_cta + wib;
+    const uint32_t tw = gridDim.x * A.warps_per_cta;
+    const uint64_t t_base = A.t0_dev ? *A.t0_dev + A.t0 : A.t0;
+    uint32_t gen = 0;
+    for (uint32_t c = 0; c < A.n; c++) {
+        const uint64_t t = t_base + c;
+        const bool pending = c > 0 || A.pending_first;
+        for (uint32_t task = warp; task < A.n_tasks; task += tw) {
+            const uint32_t G = A.n_tasks / P.n_proc;
+            const uint32_t p = A.proc_major ? task / G : task % P.n_proc;
+            const uint32_t g = A.proc_major ? task % G : task / P.n_proc;
+            uint64_t dacc = 0;
+            if (MODE == 2) {
+                const uint32_t inst = g * 32u + lane;
+                const int32_t col = DIGEST ? S.track[inst] : -1;
+                rtl_dispatch(p, Pg, Sg, g, t, pending, lane, &dacc, col);
+                if (DIGEST && col >= 0) {
+                    if (p == 0) dacc += S.rom_dig[inst];
+                    ring_add(S, t + 1, col, dacc);
+                }
+            } else {
+                const int32_t col = DIGEST ? S.track[g] : -1;
+                if (lane == 0) {
+                    rtl_dispatch(p, Pg, Sg, g, t, pending, 0, &dacc, col);
+                    if (DIGEST && col >= 0) {
+                        if (p == 0) dacc += S.rom_dig[g];
+                        ring_add(S, t + 1, col, dacc);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (A.grid_sync) {
+            const bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
+            if (!grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip)) return;
+        }
+    }
+    if (A.grid_sync && A.n > 0)
+        final_commit(P, S, t_base + A.n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                     (uint64_t)gridDim.x * blockDim.x);
+}
+
+}  // namespace rtl
+
+#define RTLSIM_GEN_KERNELS(MODE)                                                                              \
+    extern "C" __global__ void __launch_bounds__(256)                                                         \
+        rtl_gen_d0(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
+        rtl::gen_cycles<MODE, false>(P, S, A);                                                                \
+    }                                                                                                         \
+    extern "C" __global__ void __launch_bounds__(256)                                                         \
+        rtl_gen_d1(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
+        rtl::gen_cycles<MODE, true>(P, S, A);                                                                 \
+    }
+#endif

@@ -25,6 +25,10 @@ SIM_SIG_INPUT, SIM_SIG_REG = 0, 1
 SIM_MODE_AUTO, SIM_MODE_LANE_OP, SIM_MODE_LANE_INST = 0, 1, 2
 SIM_KERNEL_PERSISTENT, SIM_KERNEL_PER_CYCLE, SIM_KERNEL_PER_CYCLE_GRAPH = 0, 1, 2
 MODES = {"auto": 0, "lane_op": 1, "lane_inst": 2}
+LOWERINGS = {"bytecode": 0, "generated": 1}
+ORDERS = {"auto": 0, "group_major": 1, "process_major": 2}
+# generated-CUDA modules are cached here across processes
+os.environ.setdefault("RTLSIM_GENCACHE", os.path.join(os.path.dirname(PKG), "_build", "gencache"))
 KERNELS = {"persistent": 0, "per_cycle": 1, "graph": 2}
 
 
@@ -40,7 +44,8 @@ class sim_config(C.Structure):
         ("struct_size", C.c_uint32), ("mode", C.c_int32), ("kernel", C.c_int32),
         ("target_processes", C.c_uint32), ("warps_per_cta", C.c_uint32), ("max_slots", C.c_uint32),
         ("digest_capacity", C.c_uint32), ("timeout_ms", C.c_uint32), ("big_array_bytes", C.c_uint64),
-        ("disable_stage3", C.c_uint32), ("seed_partition", C.c_uint32), ("reserved", C.c_uint32 * 8),
+        ("disable_stage3", C.c_uint32), ("seed_partition", C.c_uint32), ("lowering", C.c_uint32),
+        ("task_order", C.c_uint32), ("reserved", C.c_uint32 * 6),
     ]
 
 
@@ -88,6 +93,7 @@ EXPORTS = {
     "sim_last_error": (C.c_char_p, []),
     "sim_netlist_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "sim_state_digests_noalloc": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sim_netlist_compile_generated": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "sim_server_config_default": (None, [C.c_void_p]),
     "sim_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -159,6 +165,10 @@ def default_config(**kw) -> sim_config:
             v = MODES[v]
         if k == "kernel" and isinstance(v, str):
             v = KERNELS[v]
+        if k == "lowering" and isinstance(v, str):
+            v = LOWERINGS[v]
+        if k == "task_order" and isinstance(v, str):
+            v = ORDERS[v]
         setattr(cfg, k, v)
     return cfg
 
@@ -178,6 +188,13 @@ class Netlist:
     def from_file(cls, path, **cfg):
         with open(path, "rb") as f:
             return cls(f.read(), **cfg)
+
+    def compile_generated(self, mode) -> dict:
+        """sim_netlist_compile_generated: build the generated-CUDA lowering (no GPU needed)."""
+        sec, cached = C.c_double(), C.c_int32()
+        m = MODES[mode] if isinstance(mode, str) else mode
+        _check(lib().sim_netlist_compile_generated(self._h, m, C.byref(sec), C.byref(cached)))
+        return {"seconds": sec.value, "cached": bool(cached.value)}
 
     def table(self, name: str) -> np.ndarray:
         which, dt = TABLES[name]

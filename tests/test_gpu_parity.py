@@ -41,9 +41,13 @@ def mid_text():
     return open(netgen.cached_netlist("mid")).read()
 
 
-def test_tiny_every_cycle_persistent(tiny_text):
+LOWERINGS = ["bytecode", "generated"]
+
+
+@pytest.mark.parametrize("lowering", LOWERINGS)
+def test_tiny_every_cycle_persistent(tiny_text, lowering):
     n = 10_000
-    nl = sim.Netlist(tiny_text, mode="lane_op", digest_capacity=n + 1)
+    nl = sim.Netlist(tiny_text, mode="lane_op", digest_capacity=n + 1, lowering=lowering)
     b = sim.Batch(nl, 1, seed=42)
     b.step(n)
     b.sync()
@@ -53,10 +57,11 @@ def test_tiny_every_cycle_persistent(tiny_text):
     assert np.array_equal(b.regs(0), ref.regs())
 
 
+@pytest.mark.parametrize("lowering", LOWERINGS)
 @pytest.mark.parametrize("kernel", ["per_cycle", "graph", "persistent"])
-def test_tiny_launch_schemes(tiny_text, kernel):
+def test_tiny_launch_schemes(tiny_text, kernel, lowering):
     n = 700      # not a multiple of the graph chunk
-    nl = sim.Netlist(tiny_text, mode="lane_op", kernel=kernel, digest_capacity=n + 1)
+    nl = sim.Netlist(tiny_text, mode="lane_op", kernel=kernel, digest_capacity=n + 1, lowering=lowering)
     b = sim.Batch(nl, 1, seed=9)
     b.step(300)
     b.step(n - 300)
@@ -65,10 +70,11 @@ def test_tiny_launch_schemes(tiny_text, kernel):
     assert first_mismatch(b.digests(0, 0, n + 1), want) is None
 
 
-def test_tiny_lane_inst_ragged_instances(tiny_text):
+@pytest.mark.parametrize("lowering", LOWERINGS)
+def test_tiny_lane_inst_ragged_instances(tiny_text, lowering):
     # 70 instances: two full 32-lane groups and a ragged tail
     n, insts = 2000, [0, 1, 31, 32, 45, 69]
-    nl = sim.Netlist(tiny_text, mode="lane_inst", digest_capacity=n + 1)
+    nl = sim.Netlist(tiny_text, mode="lane_inst", digest_capacity=n + 1, lowering=lowering)
     b = sim.Batch(nl, 70, seed=5, track=insts)
     b.step(n)
     b.sync()
@@ -80,22 +86,24 @@ def test_tiny_lane_inst_ragged_instances(tiny_text):
     assert np.array_equal(b.state_digests()[0:70:7], ref_final)
 
 
+@pytest.mark.parametrize("lowering", LOWERINGS)
 @pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
-def test_partition_invariance(tiny_text, mode):
+def test_partition_invariance(tiny_text, mode, lowering):
     n = 500
     want, _ = oracle_digests(tiny_text, 3, 0, n)
     for target, seed_part in ((1, 0), (5, 0), (33, 7), (70, 0), (16, 11)):
         nl = sim.Netlist(tiny_text, mode=mode, target_processes=target, seed_partition=seed_part,
-                         digest_capacity=n + 1)
+                         digest_capacity=n + 1, lowering=lowering)
         b = sim.Batch(nl, 32 if mode == "lane_inst" else 1, seed=3)
         b.step(n)
         b.sync()
         assert first_mismatch(b.digests(0, 0, n + 1), want) is None, (target, seed_part)
 
 
-def test_mid_single_instance(mid_text):
+@pytest.mark.parametrize("lowering", LOWERINGS)
+def test_mid_single_instance(mid_text, lowering):
     n = 3000
-    nl = sim.Netlist(mid_text, mode="lane_op", digest_capacity=n + 1)
+    nl = sim.Netlist(mid_text, mode="lane_op", digest_capacity=n + 1, lowering=lowering)
     b = sim.Batch(nl, 1, seed=42)
     b.step(n)
     b.sync()
@@ -107,10 +115,11 @@ def test_mid_single_instance(mid_text):
             assert b.peek_mem(0, m, a) == ref.mem(m, a)
 
 
-def test_mid_batched_sampled(mid_text):
+@pytest.mark.parametrize("lowering", LOWERINGS)
+def test_mid_batched_sampled(mid_text, lowering):
     n, n_inst = 300, 4096
     insts = [0, 1, 4095, 31, 32, 1000, 2047, 2048, 3071, 777, 1234, 2500, 3333, 4000, 64, 96]
-    nl = sim.Netlist(mid_text, mode="lane_inst", digest_capacity=n + 1)
+    nl = sim.Netlist(mid_text, mode="lane_inst", digest_capacity=n + 1, lowering=lowering)
     b = sim.Batch(nl, n_inst, seed=42, track=insts)
     b.step(n)
     b.sync()
@@ -167,7 +176,8 @@ def test_poke_peek_and_checkpoint(tiny_text):
     assert np.array_equal(b.regs(0), ref.regs())
 
 
-def test_memory_poke_and_rom():
+@pytest.mark.parametrize("lowering", LOWERINGS)
+def test_memory_poke_and_rom(lowering):
     text = """rtlnet 1
 reg 8 0 c
 reg 16 0 q
@@ -190,7 +200,7 @@ minit 0 3 7
 end
 """
     for mode, n_inst in (("lane_op", 1), ("lane_inst", 33)):
-        nl = sim.Netlist(text, mode=mode, digest_capacity=400)
+        nl = sim.Netlist(text, mode=mode, digest_capacity=400, lowering=lowering)
         b = sim.Batch(nl, n_inst, seed=1, track=[0, n_inst - 1])
         ref = oracle.Sim(oracle.Net(text=text), seed=1, inst=0)
         want = [ref.digest()]
@@ -206,7 +216,8 @@ end
         assert first_mismatch(got, np.array(want, dtype=np.uint64)) is None
 
 
-def test_degenerate_netlists():
+@pytest.mark.parametrize("lowering", LOWERINGS)
+def test_degenerate_netlists(lowering):
     cases = [
         # one register, no inputs, next = itself
         "rtlnet 1\nreg 64 12345\nn reg 64 0\nnext 0 0\nend\n",
@@ -220,7 +231,7 @@ def test_degenerate_netlists():
     for text in cases:
         for mode, n_inst in (("lane_op", 1), ("lane_inst", 32)):
             n = 100
-            nl = sim.Netlist(text, mode=mode, digest_capacity=n + 1)
+            nl = sim.Netlist(text, mode=mode, digest_capacity=n + 1, lowering=lowering)
             b = sim.Batch(nl, n_inst, seed=8)
             b.step(n)
             b.sync()
@@ -228,10 +239,11 @@ def test_degenerate_netlists():
             assert first_mismatch(b.digests(0, 0, n + 1), want) is None, (text, mode)
 
 
-def test_barrier_timeout_is_reported(tiny_text):
+@pytest.mark.parametrize("lowering", LOWERINGS)
+def test_barrier_timeout_is_reported(tiny_text, lowering):
     # one CTA skips its arrival: the others' bounded waits expire and the
     # step reports SIM_ERR_TIMEOUT (no fault, no unbounded wait)
-    nl = sim.Netlist(tiny_text, mode="lane_op", warps_per_cta=1)
+    nl = sim.Netlist(tiny_text, mode="lane_op", warps_per_cta=1, lowering=lowering)
     b = sim.Batch(nl, 1, seed=1)
     b.debug_skip_arrival(20)
     b.step(10)
