@@ -28,6 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "simulated cycles/s (1 instance) and instance-cycles/s (batched), p50/p99 job latency"
 UNIT = "simulated cycles/s"
+# bytes of one instance's register state (1-bit packed, 32-bit and 64-bit planes)
+STATE_BYTES_MID = 6126 / 8 + 7955 * 4 + 5927 * 8
 WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
             "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
             "100k cycles; persistent kernel, grid barrier")
@@ -161,13 +163,54 @@ def mesh_row(stream, flush):
             "processes": i["n_processes"], "max_bundles": i["max_bundles"]}
 
 
+def phase_row(text, stream, cycles=500):
+    """Decomposition of a simulated cycle of the headline workload (Eq. sim_rate)."""
+    from paper_2403_04714_gb300 import sim
+    import numpy as np
+    nl = sim.Netlist(text, mode="lane_op", phase_samples=cycles)
+    b = sim.Batch(nl, 1, seed=42, stream=stream)
+    b.step(cycles)
+    b.step(cycles)
+    ph = b.phase_times(cycles)[50:]          # skip the first cycles of the launch
+    med = np.median(ph, axis=0)
+    return {"compute_ns": float(med[0]), "sync_ns": float(med[1]), "cycle_ns": float(med[2]),
+            "note": "medians over cycles 50..500 of one persistent launch; compute = earliest CTA start "
+                    "to last CTA arrival (straggler t_comp + t_comm), sync = last arrival to last release"}
+
+
+def prng_row(stream, per_proc=(1, 8, 64), procs=1216, cycles=2000):
+    """Sec. 4.1 synchronisation experiment on GB300: independent xorshift fibers
+    (t_comm = 0), `procs` processes with 1/8/64 fibers each, one instance."""
+    from paper_2403_04714_gb300 import netgen, sim
+    import numpy as np
+    out = {}
+    for k in per_proc:
+        text = netgen.gen_prng(procs * k).to_text()
+        nl = sim.Netlist(text, mode="lane_op", target_processes=procs, phase_samples=cycles)
+        b = sim.Batch(nl, 1, seed=1, stream=stream)
+        b.step(cycles)
+        b.sync()
+        t = time.perf_counter()
+        b.step(cycles)
+        b.sync()
+        sec = time.perf_counter() - t
+        ph = np.median(b.phase_times(cycles)[100:], axis=0)
+        out[f"fibers_per_process_{k}"] = {"cycles_per_s": cycles / sec, "compute_ns": float(ph[0]),
+                                          "sync_ns": float(ph[1]), "cycle_ns": float(ph[2]),
+                                          "ctas": b.launch_info()["ctas"]}
+    return out
+
+
 def served_row(n_jobs=40):
     """Continuous batching over a seeded Poisson trace of jobs (p50/p99 latency)."""
     from paper_2403_04714_gb300 import netgen, sim
     pools = {"tiny": [netgen.gen_tiny(2000 + k).to_text() for k in range(4)],
              "mid": [open(netgen.cached_netlist("mid")).read(), netgen.gen_mid(2101).to_text()],
              "mesh_small": [open(netgen.cached_netlist("mesh_small")).read()]}
-    handles = {k: [sim.Netlist(t, mode="lane_inst") for t in v] for k, v in pools.items()}
+    handles = {k: [sim.Netlist(t, mode="lane_inst", lowering="generated") for t in v] for k, v in pools.items()}
+    for hs in handles.values():          # compile (or load from the cache) before the trace starts
+        for h in hs:
+            h.compile_generated("lane_inst")
     trace = netgen.served_trace(n_jobs=n_jobs)
     srv = sim.Server(pool_slots=1024, chunk_cycles=250)
     t0 = time.perf_counter()
@@ -244,8 +287,10 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-cycles", type=int, default=300)
     ap.add_argument("--cpu-cycles", type=int, default=3000, help="oracle sample for cpu_baseline")
-    ap.add_argument("--batched-cycles", type=int, default=100)
+    ap.add_argument("--batched-cycles", type=int, default=200)
     ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
+    ap.add_argument("--rows", default="single,batched,mesh,served",
+                    help="comma list of extra rows: single, batched, mesh, served")
     args = ap.parse_args()
     rank, world, local, dist = (0, 1, 0, None)
     if args.impl == "reference":
@@ -304,9 +349,10 @@ def main():
     del b2
 
     rows = {}
-    if not args.no_rows:
+    want = set() if args.no_rows else set(args.rows.split(","))
+    if want:
         # launch-per-cycle baseline and its graph replay, same workload
-        for kname in ("per_cycle", "graph"):
+        for kname in (("per_cycle", "graph") if "single" in want else ()):
             nlk = sim.Netlist(text, mode="lane_op", kernel=kname)
             bk = sim.Batch(nlk, 1, seed=42, stream=stream)
             cyc = min(args.cycles, 2000)
@@ -314,21 +360,31 @@ def main():
             rows[f"single_{kname}"] = {"value": 3 * cyc / (sum(msk) / 1000.0), "unit": UNIT,
                                        "cycles_timed": 3 * cyc, "kernels": lk}
             del bk, nlk
-        # batched: same netlist x 4096 instances, lane = instance
-        nlb = sim.Netlist(text, mode="lane_inst")
-        bb = sim.Batch(nlb, 4096, seed=42, stream=stream)
-        msb, lb = time_steps(bb, stream, 3, 1, args.batched_cycles, flush)
-        sec = sum(msb) / 1000.0
-        ib = nlb.info()
-        rows["batched_4096"] = {
-            "value": 3 * args.batched_cycles * 4096 / sec, "unit": "instance-cycles/s",
-            "cycles_timed": 3 * args.batched_cycles, "kernels": lb, "launch": bb.launch_info(),
-            "processes": ib["n_processes"], "ops_per_cycle": ib["n_ops"],
-            "alu_frac": ib["n_ops"] * 3 * args.batched_cycles * 4096 / sec / peak,
-        }
-        del bb, nlb
-        rows["mesh_single"] = mesh_row(stream, flush)
-        rows["served"] = served_row()
+        # batched: same netlist x 4096 instances, lane = instance, both lowerings
+        for low in (("generated", "bytecode") if "batched" in want else ()):
+            nlb = sim.Netlist(text, mode="lane_inst", lowering=low, kernel="persistent_graph")
+            comp = nlb.compile_generated("lane_inst") if low == "generated" else None
+            bb = sim.Batch(nlb, 4096, seed=42, stream=stream)
+            cyc = args.batched_cycles if low == "generated" else max(10, args.batched_cycles // 5)
+            msb, lb = time_steps(bb, stream, 3, 1, cyc, flush)
+            sec = sum(msb) / 1000.0
+            ib = nlb.info()
+            ic = 3 * cyc * 4096 / sec
+            rows[f"batched_4096_{low}"] = {
+                "value": ic, "unit": "instance-cycles/s", "cycles_timed": 3 * cyc, "kernels": lb,
+                "launch": bb.launch_info(), "processes": ib["n_processes"], "ops_per_cycle": ib["n_ops"],
+                "alu_frac": ib["n_ops"] * ic / peak,
+                "hbm_gbs_algorithmic": ic * 2 * STATE_BYTES_MID / 1e9,
+                "compile": comp,
+            }
+            del bb, nlb
+        if "single" in want:
+            rows["phases"] = phase_row(text, stream)
+            rows["prng_sync"] = prng_row(stream)
+        if "mesh" in want:
+            rows["mesh_single"] = mesh_row(stream, flush)
+        if "served" in want:
+            rows["served"] = served_row()
 
     # ---- CPU baseline: the oracle on one host core, bounded sample -------------
     cpu = None

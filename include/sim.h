@@ -67,8 +67,12 @@ enum { SIM_MODE_AUTO = 0, SIM_MODE_LANE_OP = 1, SIM_MODE_LANE_INST = 2 };
  *   PER_CYCLE:   one kernel launch per simulated cycle; the launch boundary
  *                is the barrier (the plain baseline).
  *   PER_CYCLE_GRAPH: the PER_CYCLE launch chain captured once into a CUDA
- *                graph and replayed. */
-enum { SIM_KERNEL_PERSISTENT = 0, SIM_KERNEL_PER_CYCLE = 1, SIM_KERNEL_PER_CYCLE_GRAPH = 2 };
+ *                graph and replayed.
+ *   PERSISTENT_GRAPH: the PERSISTENT launch of a step (barrier reset,
+ *                cooperative launch, cycle-base advance) captured into a CUDA
+ *                graph per step length and replayed. */
+enum { SIM_KERNEL_PERSISTENT = 0, SIM_KERNEL_PER_CYCLE = 1, SIM_KERNEL_PER_CYCLE_GRAPH = 2,
+       SIM_KERNEL_PERSISTENT_GRAPH = 3 };
 
 /* How processes are lowered.
  *   BYTECODE:  a compact 16-byte instruction stream run by one interpreter
@@ -82,14 +86,16 @@ enum { SIM_LOWER_BYTECODE = 0, SIM_LOWER_GENERATED = 1 };
 /* Task order.  GROUP_MAJOR: neighbouring warps run different processes of
  * the same instances (their state stays in L2).  PROCESS_MAJOR: neighbouring
  * warps run the same process for different instance groups (its code and
- * program stay hot in the SM).  AUTO: PROCESS_MAJOR for LANE_INST. */
-enum { SIM_ORDER_AUTO = 0, SIM_ORDER_GROUP_MAJOR = 1, SIM_ORDER_PROCESS_MAJOR = 2 };
+ * program stay hot in the SM).  CTA_MAJOR (generated LANE_INST only): each
+ * CTA runs every instance group of its processes, so a process's code is
+ * fetched by one SM.  AUTO: PROCESS_MAJOR for LANE_INST. */
+enum { SIM_ORDER_AUTO = 0, SIM_ORDER_GROUP_MAJOR = 1, SIM_ORDER_PROCESS_MAJOR = 2, SIM_ORDER_CTA_MAJOR = 3 };
 
 typedef struct sim_config {
     uint32_t struct_size;       /* sizeof(sim_config) */
     int32_t mode;               /* SIM_MODE_* */
     int32_t kernel;             /* SIM_KERNEL_* */
-    uint32_t target_processes;  /* SLB target count; 0 = one per resident warp */
+    uint32_t target_processes;  /* SLB target count; 0 = 8 per SM (LANE_OP/AUTO), 4 per SM (LANE_INST) */
     uint32_t warps_per_cta;     /* 0 = autotuned */
     uint32_t max_slots;         /* per-process value-slot cap; 0 = from the shared-memory budget */
     uint32_t digest_capacity;   /* per-cycle digest ring length in cycles; 0 = digests off */
@@ -99,7 +105,9 @@ typedef struct sim_config {
     uint32_t seed_partition;    /* testing: 0 = SLB; else a random partition with this seed */
     uint32_t lowering;          /* SIM_LOWER_BYTECODE or SIM_LOWER_GENERATED */
     uint32_t task_order;        /* SIM_ORDER_*: how (process, instance group) tasks map to warps */
-    uint32_t reserved[6];
+    uint32_t phase_samples;     /* persistent launches time their first N cycles per CTA (0 = off) */
+    uint32_t wave_groups;       /* process-major order: instance groups (of 32) per wave; 0 = fit ~64 MB of state */
+    uint32_t reserved[4];
 } sim_config;
 
 typedef struct sim_netlist_info {
@@ -231,6 +239,13 @@ void sim_free_blob(void *blob);
  * processes, tasks per cycle; and how many kernels it launched. */
 int sim_launch_info(sim_batch *b, uint32_t *ctas, uint32_t *warps_per_cta, uint32_t *tasks_per_cycle,
                     uint64_t *kernels_launched);
+
+/* Phase times of the first n cycles of the last persistent launch (needs
+ * sim_config.phase_samples >= n), in ns, three per cycle: compute (from the
+ * earliest CTA starting the cycle to the last CTA arriving at the barrier:
+ * the straggler's t_comp + t_comm, paper Eq. sim_rate), sync (last arrival
+ * to last release: t_sync) and the whole cycle.  Synchronises. */
+int sim_phase_times(sim_batch *b, uint32_t n, double *out);
 
 /* Testing hook: make one CTA skip its barrier arrival once on the next
  * persistent sim_step, so the other CTAs' bounded waits expire and the step

@@ -1,0 +1,103 @@
+"""Autotuner for the launch configuration of a netlist on this GPU.
+
+Candidates vary what the compiler cannot decide alone: the partition size
+(SLB target process count), warps per CTA (with lane = instance: instances
+per CTA = 32 x warps), the task order, and the lowering.  Each candidate is
+timed on a short run of the real workload with CUDA events; the best one is
+persisted in a JSON cache keyed by a hash of the netlist text, the instance
+count and the GPU name, so later runs reuse it without measuring.
+"""
+from __future__ import annotations
+
+import hashlib
+import json
+import os
+import time
+
+from . import sim
+
+CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build", "autotune.json")
+
+
+def _key(text: bytes, n_inst: int, device: str) -> str:
+    return hashlib.sha256(text + f"|{n_inst}|{device}".encode()).hexdigest()[:24]
+
+
+def default_candidates(n_inst: int):
+    if n_inst >= 32:
+        return [dict(mode="lane_inst", lowering="generated", warps_per_cta=w, task_order=o)
+                for w in (8, 4) for o in ("process_major", "group_major")]
+    return [dict(mode="lane_op", lowering="bytecode", warps_per_cta=w, target_processes=tp)
+            for w, tp in ((8, 0), (16, 2432), (4, 608))]
+
+
+def measure(text: bytes, n_inst: int, cfg: dict, cycles: int, seed: int = 1) -> float:
+    """Simulated instance-cycles per second of one candidate (after a warm-up step)."""
+    import torch
+    nl = sim.Netlist(text, **cfg)
+    if cfg.get("lowering") == "generated":
+        nl.compile_generated(cfg.get("mode", "lane_inst"))
+    stream = torch.cuda.Stream()
+    b = sim.Batch(nl, n_inst, seed=seed, stream=stream)
+    b.step(cycles)
+    b.sync()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    b.step(cycles)
+    e.record(stream)
+    e.synchronize()
+    sec = a.elapsed_time(e) / 1000.0
+    b.close()
+    return n_inst * cycles / sec
+
+
+def choose(results):
+    """Best candidate: highest throughput, ties to the earlier candidate."""
+    best = None
+    for cfg, v in results:
+        if best is None or v > best[1]:
+            best = (cfg, v)
+    return best
+
+
+def autotune(text: bytes | str, n_inst: int, candidates=None, cycles: int | None = None,
+             cache_path: str = CACHE, measure_fn=measure, device: str | None = None, force: bool = False) -> dict:
+    """Pick the fastest candidate configuration; returns {"config", "value", "results", "cached"}."""
+    if isinstance(text, str):
+        text = text.encode()
+    if device is None:
+        import torch
+        device = torch.cuda.get_device_name(0)
+    key = _key(text, n_inst, device)
+    cache = {}
+    if os.path.exists(cache_path):
+        try:
+            with open(cache_path) as f:
+                cache = json.load(f)
+        except (OSError, ValueError):
+            cache = {}
+    if not force and key in cache:
+        out = dict(cache[key])
+        out["cached"] = True
+        return out
+    candidates = candidates or default_candidates(n_inst)
+    cycles = cycles or (50 if n_inst >= 32 else 2000)
+    results = []
+    t0 = time.time()
+    for cfg in candidates:
+        try:
+            results.append((cfg, measure_fn(text, n_inst, cfg, cycles)))
+        except sim.SimError:               # a candidate that does not fit scores 0
+            results.append((cfg, 0.0))
+    cfg, value = choose(results)
+    out = {"config": cfg, "value": value, "results": [[c, v] for c, v in results],
+           "seconds": time.time() - t0, "device": device}
+    cache[key] = out
+    os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+    tmp = f"{cache_path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(cache, f, indent=1)
+    os.replace(tmp, cache_path)
+    out = dict(out)
+    out["cached"] = False
+    return out

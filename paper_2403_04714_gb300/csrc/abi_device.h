@@ -95,7 +95,11 @@ struct LaunchArgs {
     uint32_t prog_words;        // per-warp resident program area in 32-bit words (0 = read from global)
     uint32_t n_tasks;           // processes x instance groups
     uint32_t group;             // instances per task (1 LANE_OP, 32 LANE_INST)
-    uint32_t proc_major;        // task k = (process k / groups, group k % groups), else group-major
+    uint32_t proc_major;        // process-major task order (in waves), else group-major
+    uint32_t wave_groups;       // instance groups per wave of the process-major order (0 = all)
+    uint32_t cta_major;         // CTA c runs processes c, c+grid, ...; its warps split the groups
+    uint64_t* phase;            // per sampled cycle and CTA: {cycle start, CTA arrived, released} (ns), or null
+    uint32_t phase_n;           // cycles recorded from the start of the launch
 };
 
 }  // namespace rtl

@@ -279,6 +279,8 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
     for (uint32_t c = 0; c < A.n; c++) {
         const uint64_t t = t_base + c;
         const bool pending = c > 0 || A.pending_first;
+        uint64_t* rec = (A.phase && c < A.phase_n) ? A.phase + ((uint64_t)c * gridDim.x + blockIdx.x) * 3 : nullptr;
+        if (rec && threadIdx.x == 0) rec[0] = globaltimer_ns();
         if (resident) {
             uint32_t off = 0;
             for (uint32_t p = warp; p < P.n_proc; p += tw) {
@@ -289,16 +291,15 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
             for (uint32_t task = warp; task < A.n_tasks; task += tw) {
                 // process-major order: neighbouring warps run the same process
                 // for different instance groups (its code and constants stay hot)
-                const uint32_t G = A.n_tasks / P.n_proc;
-                uint32_t p = A.proc_major ? task / G : task % P.n_proc;
-                uint32_t g = A.proc_major ? task % G : task / P.n_proc;
+            uint32_t p, g;
+            task_coords(A, P.n_proc, task, p, g);
                 if (MODE == SIM_MODE_LANE_INST) task_lane_inst<DIGEST>(P, S, p, g, t, pending, sl, lane);
                 else task_lane_op<DIGEST>(P, S, p, g, t, pending, sl, lane);
             }
         }
         if (A.grid_sync) {
             bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
-            if (!grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip)) return;
+            if (!grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip, rec ? rec + 1 : nullptr)) return;
         }
     }
     if (A.grid_sync && A.n > 0)

@@ -136,7 +136,8 @@ struct sim_batch {
         in_w, reg_cls, reg_idx, mem_word_off;
     // state
     DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, rom_dig, bar, err, t0_dev,
-        scratch, P_dev, S_dev;
+        scratch, P_dev, S_dev, phase;
+    uint32_t phase_n = 0, phase_grid = 0;   // phase timers of the last persistent launch
     DevProg P{};
     DevState S{};
     std::vector<uint8_t> h_hold_flag;     // host mirror
@@ -148,17 +149,23 @@ struct sim_batch {
     size_t smem = 0;
     uint32_t slot_words = 0, prog_words = 0, n_tasks = 0;
     uint32_t proc_major = 0;                // task order (see LaunchArgs)
+    uint32_t wave_groups = 0;
+    uint32_t cta_major = 0;
     uint64_t kernels_launched = 0;
     int32_t skip_cta = -1;
     uint64_t timeout_ns = 2000000000ULL;
     // graph replay of per-cycle launches
     cudaGraphExec_t graph = nullptr;
     uint32_t graph_chunk = 0;
+    cudaGraphExec_t pgraph = nullptr;      // captured persistent step
+    uint64_t pgraph_n = 0;
+    DevState pgraph_state{};
     DevState graph_state{};               // state descriptor captured in the graph
     bool own_stream = false;
     ~sim_batch() {
         if (pool) rtl::pool_extra_free(pool);
         if (graph) cudaGraphExecDestroy(graph);
+        if (pgraph) cudaGraphExecDestroy(pgraph);
         if (own_stream && stream) cudaStreamDestroy(stream);
     }
     // copies ordered on the batch's stream, complete on return
@@ -212,7 +219,9 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
         pc.stage3 = !h->cfg.disable_stage3;
         pc.random_seed = h->cfg.seed_partition;
         uint32_t target = h->cfg.target_processes;
-        if (!target) target = h->cfg.mode == SIM_MODE_LANE_INST ? 512 : uint32_t(sm_count()) * 8;
+        // defaults measured on GB300: one process per warp of 8-warp CTAs for a
+        // single instance; four processes per SM with lane = instance
+        if (!target) target = uint32_t(sm_count()) * (h->cfg.mode == SIM_MODE_LANE_INST ? 4 : 8);
         pc.target = target;
         rc = partition(h->nl, pc, h->part, err);
         if (rc) return set_err(rc, err);
@@ -375,8 +384,8 @@ int plan_launch_gen(sim_batch* b) {
     b->slot_words = 0;
     b->prog_words = 0;
     b->smem = 0;
-    // generated kernels are compiled for at most 256 threads per CTA
-    int warps = std::min(8, b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8);
+    // generated kernels: up to 1024 threads per CTA at 64 registers per thread
+    int warps = std::min(32, b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8);
     b->warps = warps;
     b->threads = warps * 32;
     int occ = 0;
@@ -683,6 +692,8 @@ LaunchArgs base_args(sim_batch* b) {
     A.n_tasks = b->n_tasks;
     A.group = b->mode == SIM_MODE_LANE_INST ? 32 : 1;
     A.proc_major = b->proc_major;
+    A.wave_groups = b->wave_groups;
+    A.cta_major = b->cta_major;
     return A;
 }
 
@@ -702,6 +713,18 @@ int clear_ring(sim_batch* b, uint64_t t0, uint64_t n) {
 
 int step_persistent(sim_batch* b, uint64_t n) {
     LaunchArgs A = base_args(b);
+    if (b->nl->cfg.phase_samples) {
+        const uint32_t want = std::min<uint64_t>(b->nl->cfg.phase_samples, n);
+        const size_t bytes = size_t(b->nl->cfg.phase_samples) * b->grid * 24;
+        if (b->phase.n < bytes) {
+            int rc = b->phase.alloc(bytes);
+            if (rc) return rc;
+        }
+        A.phase = b->phase.as<uint64_t>();
+        A.phase_n = want;
+        b->phase_n = want;
+        b->phase_grid = uint32_t(b->grid);
+    }
     A.t0 = b->cycle;
     A.n = uint32_t(n);
     A.pending_first = 0;
@@ -721,6 +744,41 @@ int step_persistent(sim_batch* b, uint64_t n) {
 int per_cycle_grid(sim_batch* b) {
     if (b->prog_words) return b->grid;
     return std::max(1, int((b->n_tasks + b->warps - 1) / b->warps));
+}
+
+// The persistent step captured into a CUDA graph (one graph per step length),
+// replayed with the cycle base read from device memory.
+int step_persistent_graph(sim_batch* b, uint64_t n) {
+    int rc = sync_state_view(b);
+    if (rc) return rc;
+    if (b->skip_cta >= 0) return step_persistent(b, n);
+    if (!b->pgraph || b->pgraph_n != n || memcmp(&b->pgraph_state, &b->S, sizeof(DevState)) != 0) {
+        if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
+        b->pgraph = nullptr;
+        b->pgraph_state = b->S;
+        cudaGraph_t g;
+        CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        LaunchArgs A = base_args(b);
+        A.t0_dev = b->t0_dev.as<uint64_t>();
+        A.t0 = 0;
+        A.n = uint32_t(n);
+        A.pending_first = 0;
+        A.grid_sync = 1;
+        cudaError_t e = cudaMemsetAsync(b->bar.p, 0, 8, b->stream);
+        if (e == cudaSuccess) e = launch_any(b, true, b->grid, A);
+        if (e == cudaSuccess) e = launch_advance(b->stream, b->t0_dev.as<uint64_t>(), n);
+        cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return set_err(SIM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+        e = cudaGraphInstantiate(&b->pgraph, g, 0);
+        cudaGraphDestroy(g);
+        CUDA_TRY(e);
+        b->pgraph_n = n;
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->t0_dev.p, &b->cycle, 8, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaGraphLaunch(b->pgraph, b->stream));
+    b->kernels_launched += 2;
+    return SIM_OK;
 }
 
 int step_per_cycle(sim_batch* b, uint64_t n) {
@@ -833,8 +891,12 @@ int sim_create_instances(sim_netlist* nl, uint32_t n_inst, uint64_t seed, void* 
         b->I = b->mode == SIM_MODE_LANE_INST ? (n_inst + 31) / 32 * 32 : n_inst;
         b->timeout_ns = uint64_t(nl->cfg.timeout_ms ? nl->cfg.timeout_ms : 2000) * 1000000ULL;
         // lane = instance: process-major task order unless the config asks otherwise
-        b->proc_major = nl->cfg.task_order == SIM_ORDER_PROCESS_MAJOR ||
+        b->proc_major = nl->cfg.task_order == SIM_ORDER_PROCESS_MAJOR || nl->cfg.task_order == SIM_ORDER_CTA_MAJOR ||
                         (nl->cfg.task_order == SIM_ORDER_AUTO && b->mode == SIM_MODE_LANE_INST);
+        // waves trade code reuse for L2 reuse of the state; measured on the
+        // 4096-instance mid batch, code reuse wins (one wave of all groups)
+        b->wave_groups = nl->cfg.wave_groups;
+        b->cta_major = nl->cfg.task_order == SIM_ORDER_CTA_MAJOR;
         int rc;
         if ((rc = upload_program(b.get())) || (rc = init_state(b.get()))) return rc;
         if (nl->cfg.lowering == SIM_LOWER_GENERATED) {
@@ -883,6 +945,7 @@ int sim_step(sim_batch* b, uint64_t n_cycles) {
         if (rc) return rc;
         if (b->kernel == SIM_KERNEL_PER_CYCLE) rc = step_per_cycle(b, n);
         else if (b->kernel == SIM_KERNEL_PER_CYCLE_GRAPH) rc = step_graph(b, n);
+        else if (b->kernel == SIM_KERNEL_PERSISTENT_GRAPH) rc = step_persistent_graph(b, n);
         else rc = step_persistent(b, n);
         if (rc) return rc;
         b->cycle += n;
@@ -1182,6 +1245,28 @@ int sim_restore(sim_batch* b, const void* blob, size_t len) {
 }
 
 void sim_free_blob(void* blob) { free(blob); }
+
+int sim_phase_times(sim_batch* b, uint32_t n, double* out) {
+    if (!b || (n && !out)) return set_err(SIM_ERR_BADARG, "bad argument");
+    if (n > b->phase_n) return set_err(SIM_ERR_STATE, "fewer cycles were recorded (set sim_config.phase_samples)");
+    int rc = sim_sync(b);
+    if (rc) return rc;
+    std::vector<uint64_t> raw(size_t(n) * b->phase_grid * 3);
+    if ((rc = b->d2h(raw.data(), b->phase.p, raw.size() * 8))) return rc;
+    for (uint32_t c = 0; c < n; c++) {
+        uint64_t start = ~0ULL, arrive = 0, release = 0;
+        for (uint32_t k = 0; k < b->phase_grid; k++) {
+            const uint64_t* r = &raw[(size_t(c) * b->phase_grid + k) * 3];
+            start = std::min(start, r[0]);
+            arrive = std::max(arrive, r[1]);
+            release = std::max(release, r[2]);
+        }
+        out[c * 3 + 0] = double(arrive - start);
+        out[c * 3 + 1] = double(release - arrive);
+        out[c * 3 + 2] = double(release - start);
+    }
+    return SIM_OK;
+}
 
 int sim_launch_info(sim_batch* b, uint32_t* ctas, uint32_t* warps_per_cta, uint32_t* tasks_per_cycle,
                     uint64_t* kernels_launched) {

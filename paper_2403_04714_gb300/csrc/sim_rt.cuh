@@ -41,11 +41,15 @@ __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *(vola
 // Grid-wide barrier: arrival counter plus generation word.  Every wait is
 // bounded: past `timeout_ns`, or once another CTA has recorded an error, the
 // CTA records SIM_ERR_TIMEOUT (first error wins) and returns false.
-static __device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeout_ns, int32_t* err, bool skip) {
+// With `rec` set, thread 0 stores the time the whole CTA arrived (rec[0]) and
+// the time the barrier released it (rec[1]), from %globaltimer.
+static __device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeout_ns, int32_t* err, bool skip,
+                                    uint64_t* rec = nullptr) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
+        if (rec) rec[0] = globaltimer_ns();
         __threadfence();
         if (!skip) {
             uint32_t arrived = atomicAdd(&bar[0], 1u);
@@ -66,6 +70,7 @@ static __device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeo
         }
         gen++;
         __threadfence();
+        if (rec) rec[1] = globaltimer_ns();
         s_ok = ok;
     }
     __syncthreads();
@@ -142,6 +147,26 @@ __device__ __forceinline__ void mem_digest_update(const DevState& S, uint32_t m,
     ring_add(S, t, col, v);
 }
 
+// Task k -> (process p, instance group g).  Group-major: the processes of one
+// group are neighbours.  Process-major in waves: the groups are split into
+// waves of `wave_groups` (whose state fits in L2); within a wave the tasks of
+// one process are neighbours, so warps that run together share its code.
+__device__ __forceinline__ void task_coords(const LaunchArgs& A, uint32_t n_proc, uint32_t task, uint32_t& p,
+                                            uint32_t& g) {
+    if (!A.proc_major) {
+        p = task % n_proc;
+        g = task / n_proc;
+        return;
+    }
+    const uint32_t G = A.n_tasks / n_proc;
+    const uint32_t W = A.wave_groups ? (A.wave_groups < G ? A.wave_groups : G) : G;
+    const uint32_t per_wave = W * n_proc;
+    const uint32_t wave = task / per_wave, r = task % per_wave;
+    const uint32_t gw = (wave + 1) * W <= G ? W : G - wave * W;    // the last wave may be short
+    p = r / gw;
+    g = wave * W + r % gw;
+}
+
 // Apply the last cycle's write records after the final barrier of a launch
 // (or in a launch of its own after per-cycle launches).
 static __device__ void final_commit(const DevProg& P, const DevState& S, uint64_t t_end, uint64_t gtid,
@@ -186,10 +211,25 @@ __device__ __forceinline__ void gen_cycles(const DevProg* __restrict__ Pg, const
     for (uint32_t c = 0; c < A.n; c++) {
         const uint64_t t = t_base + c;
         const bool pending = c > 0 || A.pending_first;
-        for (uint32_t task = warp; task < A.n_tasks; task += tw) {
-            const uint32_t G = A.n_tasks / P.n_proc;
-            const uint32_t p = A.proc_major ? task / G : task % P.n_proc;
-            const uint32_t g = A.proc_major ? task % G : task / P.n_proc;
+        uint64_t* rec = (A.phase && c < A.phase_n) ? A.phase + ((uint64_t)c * gridDim.x + blockIdx.x) * 3 : nullptr;
+        if (rec && threadIdx.x == 0) rec[0] = globaltimer_ns();
+        const uint32_t G = A.n_tasks / P.n_proc;
+        const uint32_t n_iter = A.cta_major ? ((P.n_proc + gridDim.x - 1) / gridDim.x) *
+                                                  ((G + A.warps_per_cta - 1) / A.warps_per_cta)
+                                            : (A.n_tasks + tw - 1) / tw;
+        for (uint32_t it = 0; it < n_iter; it++) {
+            uint32_t p, g;
+            if (A.cta_major) {
+                // CTA-major: all groups of one process stay on one CTA (one SM)
+                const uint32_t gper = (G + A.warps_per_cta - 1) / A.warps_per_cta;
+                p = blockIdx.x + (it / gper) * gridDim.x;
+                g = wib + (it % gper) * A.warps_per_cta;
+                if (p >= P.n_proc || g >= G) continue;
+            } else {
+                const uint32_t task = warp + it * tw;
+                if (task >= A.n_tasks) break;
+                task_coords(A, P.n_proc, task, p, g);
+            }
             uint64_t dacc = 0;
             if (MODE == 2) {
                 const uint32_t inst = g * 32u + lane;
@@ -213,7 +253,7 @@ __device__ __forceinline__ void gen_cycles(const DevProg* __restrict__ Pg, const
         }
         if (A.grid_sync) {
             const bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
-            if (!grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip)) return;
+            if (!grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip, rec ? rec + 1 : nullptr)) return;
         }
     }
     if (A.grid_sync && A.n > 0)
@@ -224,11 +264,11 @@ __device__ __forceinline__ void gen_cycles(const DevProg* __restrict__ Pg, const
 }  // namespace rtl
 
 #define RTLSIM_GEN_KERNELS(MODE)                                                                              \
-    extern "C" __global__ void __launch_bounds__(256)                                                         \
+    extern "C" __global__ void __launch_bounds__(1024)                                                        \
         rtl_gen_d0(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
         rtl::gen_cycles<MODE, false>(P, S, A);                                                                \
     }                                                                                                         \
-    extern "C" __global__ void __launch_bounds__(256)                                                         \
+    extern "C" __global__ void __launch_bounds__(1024)                                                        \
         rtl_gen_d1(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
         rtl::gen_cycles<MODE, true>(P, S, A);                                                                 \
     }

@@ -561,6 +561,21 @@ def gen_mesh(seed=1002, mesh=4, ops_per_block=120_000, regs_per_block=8_000, dep
     return nl
 
 
+def gen_prng(n_fibers: int, seed: int = 5) -> Netlist:
+    """Independent 64-bit xorshift generators (three XORs, three shifts each):
+    one fiber per register, no value crosses fibers (the synchronisation
+    experiment's circuit, Sec. 4.1)."""
+    rng = random.Random(seed)
+    nl = Netlist()
+    for i in range(n_fibers):
+        r = nl.add_reg(64, rng.getrandbits(64) | 1)
+        x = nl.node("reg", 64, r)
+        for sh, kind in ((13, "shl"), (7, "shr"), (17, "shl")):
+            x = nl.node("xor", 64, x, nl.node(kind, 64, x, nl.node("const", 7, sh)))
+        nl.set_next(r, x)
+    return nl
+
+
 def gen_mesh_small(seed=1003) -> Netlist:
     """A 2x2 mesh of 30k-op blocks: the mesh shape at served-job scale."""
     return gen_mesh(seed, mesh=2, ops_per_block=30_000, regs_per_block=2_000, depth=40, inputs_per_block=8)

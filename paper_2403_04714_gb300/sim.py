@@ -26,10 +26,10 @@ SIM_MODE_AUTO, SIM_MODE_LANE_OP, SIM_MODE_LANE_INST = 0, 1, 2
 SIM_KERNEL_PERSISTENT, SIM_KERNEL_PER_CYCLE, SIM_KERNEL_PER_CYCLE_GRAPH = 0, 1, 2
 MODES = {"auto": 0, "lane_op": 1, "lane_inst": 2}
 LOWERINGS = {"bytecode": 0, "generated": 1}
-ORDERS = {"auto": 0, "group_major": 1, "process_major": 2}
+ORDERS = {"auto": 0, "group_major": 1, "process_major": 2, "cta_major": 3}
 # generated-CUDA modules are cached here across processes
 os.environ.setdefault("RTLSIM_GENCACHE", os.path.join(os.path.dirname(PKG), "_build", "gencache"))
-KERNELS = {"persistent": 0, "per_cycle": 1, "graph": 2}
+KERNELS = {"persistent": 0, "per_cycle": 1, "graph": 2, "persistent_graph": 3}
 
 
 class SimError(RuntimeError):
@@ -45,7 +45,8 @@ class sim_config(C.Structure):
         ("target_processes", C.c_uint32), ("warps_per_cta", C.c_uint32), ("max_slots", C.c_uint32),
         ("digest_capacity", C.c_uint32), ("timeout_ms", C.c_uint32), ("big_array_bytes", C.c_uint64),
         ("disable_stage3", C.c_uint32), ("seed_partition", C.c_uint32), ("lowering", C.c_uint32),
-        ("task_order", C.c_uint32), ("reserved", C.c_uint32 * 6),
+        ("task_order", C.c_uint32), ("phase_samples", C.c_uint32), ("wave_groups", C.c_uint32),
+        ("reserved", C.c_uint32 * 4),
     ]
 
 
@@ -94,6 +95,7 @@ EXPORTS = {
     "sim_netlist_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "sim_state_digests_noalloc": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_netlist_compile_generated": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
+    "sim_phase_times": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "sim_server_config_default": (None, [C.c_void_p]),
     "sim_server_create": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_submit": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -331,6 +333,12 @@ class Batch:
 
     def restore(self, blob: bytes):
         _check(lib().sim_restore(self._h, blob, len(blob)))
+
+    def phase_times(self, n: int) -> np.ndarray:
+        """sim_phase_times: per cycle (compute ns, sync ns, cycle ns) of the last persistent launch."""
+        out = np.zeros((max(n, 1), 3), dtype=np.float64)
+        _check(lib().sim_phase_times(self._h, n, out.ctypes.data))
+        return out[:n]
 
     def launch_info(self) -> dict:
         a, b, c, d = C.c_uint32(), C.c_uint32(), C.c_uint32(), C.c_uint64()

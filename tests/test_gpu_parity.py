@@ -58,7 +58,7 @@ def test_tiny_every_cycle_persistent(tiny_text, lowering):
 
 
 @pytest.mark.parametrize("lowering", LOWERINGS)
-@pytest.mark.parametrize("kernel", ["per_cycle", "graph", "persistent"])
+@pytest.mark.parametrize("kernel", ["per_cycle", "graph", "persistent", "persistent_graph"])
 def test_tiny_launch_schemes(tiny_text, kernel, lowering):
     n = 700      # not a multiple of the graph chunk
     nl = sim.Netlist(tiny_text, mode="lane_op", kernel=kernel, digest_capacity=n + 1, lowering=lowering)
@@ -119,9 +119,12 @@ def test_mid_single_instance(mid_text, lowering):
 def test_mid_batched_sampled(mid_text, lowering):
     n, n_inst = 300, 4096
     insts = [0, 1, 4095, 31, 32, 1000, 2047, 2048, 3071, 777, 1234, 2500, 3333, 4000, 64, 96]
-    nl = sim.Netlist(mid_text, mode="lane_inst", digest_capacity=n + 1, lowering=lowering)
+    nl = sim.Netlist(mid_text, mode="lane_inst", digest_capacity=n + 1, lowering=lowering,
+                     kernel="persistent_graph")
     b = sim.Batch(nl, n_inst, seed=42, track=insts)
-    b.step(n)
+    b.step(100)
+    b.step(100)
+    b.step(n - 200)
     b.sync()
     wants = oracle_many(mid_text, 42, insts, n)
     for i, want in zip(insts, wants):
