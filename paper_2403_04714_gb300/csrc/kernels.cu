@@ -149,11 +149,37 @@ __device__ void task_lane_inst(const DevProg& P, const DevState& S, uint32_t p, 
 // ---------------------------------------------------------------------------
 // LANE_OP: one warp, one process, one instance; lanes run a 32-wide step.
 // ---------------------------------------------------------------------------
+// All 13 operators without branches: every candidate result is formed and the
+// opcode selects one, so lanes running different operators in one schedule
+// step follow a single instruction path (no serialised divergent paths).
+__device__ __forceinline__ uint64_t alu_select(uint32_t op, uint64_t a, uint64_t b, uint64_t c, uint32_t x) {
+    const bool big = b >= 64;
+    const uint32_t s = uint32_t(b) & 63u;
+    uint64_t r = a + b;
+    r = op == D_SUB ? a - b : r;
+    r = op == D_MUL ? a * b : r;
+    r = op == D_AND ? (a & b) : r;
+    r = op == D_OR ? (a | b) : r;
+    r = op == D_XOR ? (a ^ b) : r;
+    r = op == D_SHL ? (big ? 0ull : a << s) : r;
+    r = op == D_SHR ? (big ? 0ull : a >> s) : r;
+    r = op == D_EQ ? (uint64_t)(a == b) : r;
+    r = op == D_LT ? (uint64_t)(a < b) : r;
+    r = op == D_MUX ? (a != 0 ? b : c) : r;
+    r = op == D_SLICE ? (a >> (x & 63u)) : r;
+    r = op == D_CONCAT ? ((a << (x & 63u)) | b) : r;
+    return r;
+}
+
 template <bool DIGEST>
 __device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, const DevState& S, uint32_t inst, uint64_t t,
                                              uint64_t key, int32_t col, bool pending, uint64_t* __restrict__ sl,
                                              uint64_t& dacc) {
     const uint32_t par = uint32_t(t & 1), nxt = par ^ 1;
+    if (d.op >= D_ADD && d.op <= D_CONCAT) {
+        sl[d.dst] = alu_select(d.op, sl[d.a], sl[d.b], sl[d.c], d.x) & wmask(d.w);
+        return;
+    }
     switch (d.op) {
     case D_NOP:
         break;
