@@ -35,6 +35,12 @@ struct DIns {
     uint32_t imm;
 };
 
+// LANE_OP step word of a shared-memory program: first instruction (bits
+// 0-15), instruction count (bits 16-21), and this flag when the step holds
+// anything other than the 13 operators (leaves, memory reads, stores).
+constexpr uint32_t kStepGeneric = 1u << 31;
+constexpr uint32_t kStepCountMask = 0x3fu;
+
 // Program tables of one lowered netlist (device pointers).
 struct DevProg {
     const DIns* s_ins;          // LANE_OP bundles (32 instructions per row)

@@ -723,6 +723,7 @@ struct Item {
     int32_t id;        // node id / register / port / memory
     int level;
     uint8_t op;        // for sorting within a level
+    int phase = 0;     // LANE_OP order: 0 leaves and commits, 1 operators, 2 stores and write records
 };
 
 constexpr uint16_t kNoSlot = 0xffff;
@@ -788,8 +789,20 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
                 }
             }
         }
-        // steps: by level, then operator kind (less divergence in a step), then id
+        // steps: leaves and memory commits first, then the operators by level,
+        // then register stores and write records (their values stay in slots
+        // until the end); within a level by operator kind (less divergence in a
+        // step), then id.  Operator steps hold operators only, apart from the
+        // rare memory reads, so the interpreter runs them without branches.
+        auto phase = [&](const Item& it) {
+            if (it.kind == 1 || it.kind == 2) return 2;
+            if (it.kind == 3) return 0;
+            const uint8_t op = nl.nodes[it.id].op;
+            return (op == OP_INPUT || op == OP_REG || op == OP_CONST) ? 0 : 1;
+        };
+        for (auto& it : items) it.phase = phase(it);
         std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
+            if (a.phase != b.phase) return a.phase < b.phase;
             if (a.level != b.level) return a.level < b.level;
             if (a.op != b.op) return a.op < b.op;
             if (a.kind != b.kind) return a.kind < b.kind;
@@ -799,13 +812,17 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
         std::vector<uint32_t> bundle(items.size());
         uint32_t nb = 0;
         {
-            int cur_level = -1;
+            int cur_level = -1, cur_phase = -1;
             uint32_t fill = 0;
             for (size_t i = 0; i < items.size(); i++) {
-                if (items[i].level != cur_level || fill == 32) {
+                // operators never share a step with their own operands; the
+                // leaves and the stores have no dependences among themselves
+                const int lv = items[i].phase == 1 ? items[i].level : 0;
+                if (lv != cur_level || items[i].phase != cur_phase || fill == 32) {
                     nb++;
                     fill = 0;
-                    cur_level = items[i].level;
+                    cur_level = lv;
+                    cur_phase = items[i].phase;
                 }
                 bundle[i] = nb - 1;
                 fill++;
@@ -926,8 +943,10 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             std::vector<uint32_t> prog(table_words, 0);
             uint32_t first = 0;
             for (uint32_t b = 0; b < nb; b++) {
-                prog[b] = first | (count[b] << 16);
                 const DIns* row = &out.s_ins[(size_t(out.s_off[p]) + b) * 32];
+                bool operators_only = true;
+                for (uint32_t l = 0; l < count[b]; l++) operators_only &= row[l].op >= D_ADD && row[l].op <= D_CONCAT;
+                prog[b] = first | (count[b] << 16) | (operators_only ? 0u : kStepGeneric);
                 for (uint32_t l = 0; l < count[b]; l++) {
                     uint32_t w[4];
                     memcpy(w, &row[l], 16);

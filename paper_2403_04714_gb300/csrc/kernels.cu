@@ -259,11 +259,15 @@ __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, ui
 }
 
 // Program resident in shared memory: `prog` holds the step table (first
-// instruction | count << 16) followed by the instructions, 16-byte aligned.
+// instruction | count << 16 | kStepGeneric) followed by the instructions,
+// 16-byte aligned.  Operator-only steps run on all 32 lanes without a branch:
+// lanes past the step's count repeat its first instruction and write the
+// spare slot `dummy` (the last word of the warp's slot region), which no
+// instruction reads.
 template <bool DIGEST>
 __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t,
                                  bool pending, uint64_t* __restrict__ sl, const uint32_t* __restrict__ prog,
-                                 uint32_t lane) {
+                                 uint32_t lane, uint32_t dummy) {
     const uint64_t key = S.key[inst];
     const int32_t col = DIGEST ? S.track[inst] : -1;
     uint64_t dacc = 0;
@@ -272,8 +276,14 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     uint32_t e = nb ? prog[0] : 0;
     for (uint32_t b = 0; b < nb; b++) {
         const uint32_t e_next = b + 1 < nb ? prog[b + 1] : 0;
-        const uint32_t first = e & 0xffff, cnt = e >> 16;
-        if (lane < cnt) exec_lane_op<DIGEST>(decode(ins[first + lane]), P, S, inst, t, key, col, pending, sl, dacc);
+        const uint32_t first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
+        if (e & kStepGeneric) {
+            if (lane < cnt) exec_lane_op<DIGEST>(decode(ins[first + lane]), P, S, inst, t, key, col, pending, sl, dacc);
+        } else {
+            const bool on = lane < cnt;
+            const Dec d = decode(ins[on ? first + lane : first]);
+            sl[on ? d.dst : dummy] = alu_select(d.op, sl[d.a], sl[d.b], sl[d.c], d.x) & wmask(d.w);
+        }
         __syncwarp();
         e = e_next;
     }
@@ -310,7 +320,8 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
         if (resident) {
             uint32_t off = 0;
             for (uint32_t p = warp; p < P.n_proc; p += tw) {
-                for (uint32_t g = 0; g < S.I; g++) task_lane_op_res<DIGEST>(P, S, p, g, t, pending, sl, prog + off, lane);
+                for (uint32_t g = 0; g < S.I; g++)
+                    task_lane_op_res<DIGEST>(P, S, p, g, t, pending, sl, prog + off, lane, A.slot_words - 1);
                 off += P.c_size[p];
             }
         } else {

@@ -442,7 +442,7 @@ int plan_launch(sim_batch* b) {
         b->slot_words = L.max_b_slots * 32;
         b->n_tasks = n_proc * (b->I / 32);
     } else {
-        b->slot_words = (L.max_s_slots + 1) & ~1u;
+        b->slot_words = (L.max_s_slots + 2) & ~1u;   // at least one spare slot (the operator steps' dummy)
         b->n_tasks = n_proc * b->I;
     }
     size_t slot_bytes = size_t(b->slot_words) * 8;

@@ -40,7 +40,7 @@ class Emu:
                 ins = prog[(nb + 3) // 4 * 4:].copy().view(DINS)
                 self.off.append(len(rows) // 32)
                 for e in table:
-                    first, cnt = int(e) & 0xffff, int(e) >> 16
+                    first, cnt = int(e) & 0xffff, (int(e) >> 16) & 0x3f
                     row = np.zeros(32, dtype=DINS)
                     row[:cnt] = ins[first:first + cnt]
                     rows.extend(row)
