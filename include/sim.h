@@ -107,7 +107,11 @@ typedef struct sim_config {
     uint32_t task_order;        /* SIM_ORDER_*: how (process, instance group) tasks map to warps */
     uint32_t phase_samples;     /* persistent launches time their first N cycles per CTA (0 = off) */
     uint32_t wave_groups;       /* process-major order: instance groups (of 32) per wave; 0 = fit ~64 MB of state */
-    uint32_t reserved[4];
+    uint32_t cluster_size;      /* 0 = off; 2..16: thread-block clusters of this many CTAs exchange register values
+                                 * through distributed shared memory (LANE_OP, bytecode, persistent kernel, one
+                                 * instance; see sim_create_instances).  A grid of one cluster synchronises with
+                                 * the cluster's barrier instead of the grid barrier. */
+    uint32_t reserved[3];
 } sim_config;
 
 typedef struct sim_netlist_info {
@@ -162,6 +166,12 @@ int sim_netlist_compile_generated(sim_netlist *nl, int32_t mode, double *seconds
  *     a step table, first instruction | count << 16, padded to 4 words, then
  *     the 16-byte instructions)                    15 first word of each (u32)
  *  16 words of each (u32)
+ *  Cluster exchange (cluster_size > 0; empty otherwise):
+ *  17 process of each warp of the grid (u32, 0xffffffff = idle)
+ *  18 first mirror entry of each CTA (u32, grid + 1 offsets)
+ *  19 register held by each mirror entry (u32)
+ *  20 {CTAs per cluster, warps per CTA, grid CTAs, mirror entries per CTA, cross-process register reads
+ *      inside a cluster, reads across clusters} (u64 x 6)
  * Errors: BADARG. */
 int sim_netlist_table(const sim_netlist *nl, int32_t which, void *out, size_t *bytes);
 
@@ -169,7 +179,10 @@ int sim_netlist_table(const sim_netlist *nl, int32_t which, void *out, size_t *b
  * netlist's register init values and memory images, cycle 0.  Instance i's
  * stimulus key is output i+1 of the SplitMix64 stream seeded with `seed`.
  * `cuda_stream` is a cudaStream_t (NULL = legacy default stream); every
- * device operation of the batch is ordered on it.  Errors: BADARG, OOM, CUDA. */
+ * device operation of the batch is ordered on it.  A netlist loaded with
+ * cluster_size > 0 takes n_inst == 1 and runs the persistent kernel as a
+ * cluster launch; CAPACITY if its clusters cannot all be resident at once.
+ * Errors: BADARG, OOM, CAPACITY, CUDA. */
 int sim_create_instances(sim_netlist *nl, uint32_t n_inst, uint64_t seed, void *cuda_stream,
                          sim_batch **out);
 void sim_batch_destroy(sim_batch *b);

@@ -26,7 +26,10 @@ enum DOp : uint8_t {
     D_NOP = 0, D_LDR, D_LDI, D_CONST, D_MEMRD,
     D_ADD, D_SUB, D_MUL, D_AND, D_OR, D_XOR, D_SHL, D_SHR, D_EQ, D_LT,
     D_MUX, D_SLICE, D_CONCAT,
-    D_STR, D_WREC, D_COMMIT, D_COUNT
+    D_STR, D_WREC, D_COMMIT,
+    D_LDM,      // register value from this CTA's mirror (cluster exchange)
+    D_STX,      // next register value into a cluster peer's mirror
+    D_COUNT
 };
 
 struct DIns {
@@ -60,8 +63,14 @@ struct DevProg {
     const uint8_t* in_w;
     const uint8_t* reg_cls;
     const uint32_t* reg_idx;
+    // cluster exchange (null unless the netlist was lowered for clusters)
+    const uint32_t* warp_proc;  // process of each warp of the grid, kNoProc if idle
+    const uint32_t* mir_off;    // per CTA: first mirror entry (grid+1 offsets)
+    const uint32_t* mir_reg;    // register held by each mirror entry
     uint32_t n_proc, n_in, n_reg, n_mem, n_wport;
 };
+
+constexpr uint32_t kNoProc = 0xffffffffu;
 
 // State of one batch of instances (device pointers).
 struct DevState {
@@ -106,6 +115,9 @@ struct LaunchArgs {
     uint32_t cta_major;         // CTA c runs processes c, c+grid, ...; its warps split the groups
     uint64_t* phase;            // per sampled cycle and CTA: {cycle start, CTA arrived, released} (ns), or null
     uint32_t phase_n;           // cycles recorded from the start of the launch
+    uint32_t cluster;           // CTAs per thread-block cluster (0 = no cluster exchange)
+    uint32_t mirror_words;      // per-CTA mirror entries per buffer (64-bit words)
+    uint32_t one_cluster;       // the grid is one cluster: cluster barrier instead of the grid barrier
 };
 
 }  // namespace rtl

@@ -1042,4 +1042,291 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
     return SIM_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Cluster placement and exchange lowering
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Step {
+    uint32_t flags = 0;
+    std::vector<DIns> ins;
+};
+
+// Steps of process p from its compact program.
+std::vector<Step> read_steps(const Lowered& low, size_t p) {
+    const uint32_t* w = low.c_words.data() + low.c_off[p];
+    const uint32_t nb = low.s_len[p], tw = (nb + 3) & ~3u;
+    const DIns* ins = reinterpret_cast<const DIns*>(w + tw);
+    std::vector<Step> steps(nb);
+    for (uint32_t b = 0; b < nb; b++) {
+        const uint32_t e = w[b], first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
+        steps[b].flags = e & kStepGeneric;
+        steps[b].ins.assign(ins + first, ins + first + cnt);
+    }
+    return steps;
+}
+
+}  // namespace
+
+int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_t W, Lowered& low, ClusterPlan& plan,
+                   std::string& err) {
+    const size_t NP = part.procs.size();
+    if (C < 1 || W < 1 || NP == 0) { err = "cluster lowering: bad geometry"; return SIM_ERR_BADARG; }
+    const uint32_t G = C * W;                                   // processes per cluster
+    const uint32_t n_groups = uint32_t((NP + G - 1) / G);
+    plan = ClusterPlan();
+    plan.C = C;
+    plan.W = W;
+    plan.grid = n_groups * C;
+
+    // producer process of every register, and the registers each process reads
+    std::vector<int32_t> proc_of_reg(nl.reg_w.size(), -1);
+    for (size_t p = 0; p < NP; p++)
+        for (int32_t f : part.procs[p])
+            if (part.fibers[f].reg >= 0) proc_of_reg[part.fibers[f].reg] = int32_t(p);
+    std::vector<std::vector<Step>> steps(NP);
+    std::vector<std::vector<uint32_t>> reads(NP);
+    for (size_t p = 0; p < NP; p++) {
+        steps[p] = read_steps(low, p);
+        for (auto& st : steps[p])
+            for (auto& d : st.ins)
+                if (d.op == D_LDR) reads[p].push_back(d.imm);
+    }
+
+    // affinity between processes: register values passed either way
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> adj(NP);
+    {
+        std::vector<std::pair<uint32_t, uint32_t>> edges;
+        for (size_t p = 0; p < NP; p++)
+            for (uint32_t r : reads[p]) {
+                int32_t q = proc_of_reg[r];
+                if (q >= 0 && size_t(q) != p)
+                    edges.push_back({uint32_t(std::min<size_t>(p, q)), uint32_t(std::max<size_t>(p, q))});
+            }
+        std::sort(edges.begin(), edges.end());
+        for (size_t i = 0; i < edges.size();) {
+            size_t j = i;
+            while (j < edges.size() && edges[j] == edges[i]) j++;
+            adj[edges[i].first].push_back({edges[i].second, uint32_t(j - i)});
+            adj[edges[i].second].push_back({edges[i].first, uint32_t(j - i)});
+            i = j;
+        }
+    }
+    // placement: two streaming greedy passes (linear deterministic greedy:
+    // each process joins the cluster holding most of its partners, discounted
+    // by how full it is), one in breadth-first order of the communication
+    // graph and one in process order; the better one is refined by swaps
+    std::vector<uint64_t> weight(NP, 0);
+    for (size_t p = 0; p < NP; p++)
+        for (auto& e : adj[p]) weight[p] += e.second;
+    auto local_weight = [&](const std::vector<int32_t>& grp) {
+        uint64_t v = 0;
+        for (size_t p = 0; p < NP; p++)
+            for (auto& e : adj[p])
+                if (grp[p] == grp[e.first]) v += e.second;
+        return v / 2;
+    };
+    auto ldg = [&](const std::vector<uint32_t>& order) {
+        std::vector<int32_t> grp(NP, -1);
+        std::vector<uint32_t> size(n_groups, 0);
+        std::vector<double> score(n_groups, 0.0);
+        for (uint32_t p : order) {
+            std::fill(score.begin(), score.end(), 0.0);
+            for (auto& e : adj[p])
+                if (grp[e.first] >= 0) score[grp[e.first]] += e.second;
+            int32_t best = -1;
+            double best_v = -1.0;
+            for (uint32_t g = 0; g < n_groups; g++) {
+                if (size[g] >= G) continue;
+                double v = score[g] * (1.0 - double(size[g]) / G);
+                if (v > best_v || (v == best_v && size[g] < size[best])) {
+                    best = int32_t(g);
+                    best_v = v;
+                }
+            }
+            grp[p] = best;
+            size[best]++;
+        }
+        return grp;
+    };
+    std::vector<uint32_t> bfs;
+    {
+        std::vector<uint8_t> seen(NP, 0);
+        std::vector<uint32_t> by_weight(NP);
+        std::iota(by_weight.begin(), by_weight.end(), 0u);
+        std::stable_sort(by_weight.begin(), by_weight.end(), [&](uint32_t a, uint32_t b) { return weight[a] > weight[b]; });
+        for (uint32_t root : by_weight) {
+            if (seen[root]) continue;
+            size_t head = bfs.size();
+            bfs.push_back(root);
+            seen[root] = 1;
+            while (head < bfs.size()) {
+                uint32_t p = bfs[head++];
+                auto nb = adj[p];
+                std::stable_sort(nb.begin(), nb.end(), [](auto& a, auto& b) { return a.second > b.second; });
+                for (auto& e : nb)
+                    if (!seen[e.first]) {
+                        seen[e.first] = 1;
+                        bfs.push_back(e.first);
+                    }
+            }
+        }
+    }
+    std::vector<uint32_t> ident(NP);
+    std::iota(ident.begin(), ident.end(), 0u);
+    std::vector<int32_t> group = ldg(bfs);
+    {
+        std::vector<int32_t> g2 = ldg(ident);
+        if (local_weight(g2) > local_weight(group)) group = g2;
+    }
+    // swap refinement: exchange two processes of different clusters when that
+    // raises the weight kept inside clusters
+    {
+        auto gain_to = [&](uint32_t p, int32_t g) {   // partners of p in cluster g
+            uint64_t v = 0;
+            for (auto& e : adj[p])
+                if (group[e.first] == g) v += e.second;
+            return v;
+        };
+        for (int pass = 0; pass < 4; pass++) {
+            bool moved = false;
+            for (uint32_t p = 0; p < NP; p++) {
+                if (adj[p].empty()) continue;
+                // the cluster p is most connected to
+                std::unordered_map<int32_t, uint64_t> w;
+                for (auto& e : adj[p]) w[group[e.first]] += e.second;
+                const int32_t gp = group[p];
+                const uint64_t own = w.count(gp) ? w[gp] : 0;
+                int32_t gb = gp;
+                uint64_t wb = own;
+                for (auto& [g, v] : w)
+                    if (v > wb) { gb = g; wb = v; }
+                if (gb == gp) continue;
+                // the process q of gb whose move to p's cluster gains most
+                int64_t best_gain = 0;
+                int32_t best_q = -1;
+                for (uint32_t q = 0; q < NP; q++) {
+                    if (group[q] != gb) continue;
+                    int64_t pq = 0;
+                    for (auto& e : adj[p])
+                        if (e.first == q) pq = e.second;
+                    const int64_t gain = int64_t(wb) - int64_t(own) + int64_t(gain_to(q, gp)) - int64_t(gain_to(q, gb)) - 2 * pq;
+                    if (gain > best_gain) { best_gain = gain; best_q = int32_t(q); }
+                }
+                if (best_q >= 0) {
+                    group[best_q] = gp;
+                    group[p] = gb;
+                    moved = true;
+                }
+            }
+            if (!moved) break;
+        }
+    }
+    std::vector<std::vector<uint32_t>> members(n_groups);
+    for (uint32_t p = 0; p < NP; p++) members[group[p]].push_back(p);
+    plan.warp_proc.assign(size_t(plan.grid) * W, kNoProc);
+    std::vector<uint32_t> cta_of(NP);
+    for (uint32_t g = 0; g < n_groups; g++)
+        for (size_t k = 0; k < members[g].size(); k++) {
+            plan.warp_proc[size_t(g) * G + k] = members[g][k];
+            cta_of[members[g][k]] = uint32_t((size_t(g) * G + k) / W);
+        }
+
+    // mirrors: per CTA, the registers its processes read from producers of
+    // the same cluster (own CTA included)
+    std::vector<std::vector<uint32_t>> mir(plan.grid);
+    for (size_t p = 0; p < NP; p++) {
+        const uint32_t c = cta_of[p];
+        for (uint32_t r : reads[p]) {
+            int32_t q = proc_of_reg[r];
+            bool local = q >= 0 && cta_of[q] / C == c / C;
+            if (q >= 0 && size_t(q) != p) (local ? plan.reads_local : plan.reads_remote)++;
+            if (local) mir[c].push_back(r);
+        }
+    }
+    std::vector<std::unordered_map<uint32_t, uint32_t>> mir_idx(plan.grid);
+    std::vector<std::vector<std::pair<uint32_t, uint32_t>>> consumers(nl.reg_w.size());   // (CTA, entry)
+    plan.mir_off.assign(plan.grid + 1, 0);
+    for (uint32_t c = 0; c < plan.grid; c++) {
+        auto& v = mir[c];
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+        plan.mir_off[c + 1] = plan.mir_off[c] + uint32_t(v.size());
+        plan.mirror_words = std::max<uint32_t>(plan.mirror_words, uint32_t(v.size()));
+        for (size_t i = 0; i < v.size(); i++) {
+            mir_idx[c][v[i]] = uint32_t(i);
+            consumers[v[i]].push_back({c, uint32_t(i)});
+            plan.mir_reg.push_back(v[i]);
+        }
+    }
+    if (plan.mirror_words > 0xffffff) { err = "cluster mirror too large"; return SIM_ERR_CAPACITY; }
+
+    // rewrite: local reads from the mirror, mirror writes after the stores
+    for (size_t p = 0; p < NP; p++) {
+        const uint32_t c = cta_of[p];
+        std::vector<DIns> stx;
+        for (auto& st : steps[p])
+            for (auto& d : st.ins) {
+                if (d.op == D_LDR) {
+                    auto it = mir_idx[c].find(d.imm);
+                    if (it == mir_idx[c].end()) continue;
+                    d.op = D_LDM;
+                    d.c = 0;
+                    d.b = uint16_t(it->second & 0xffff);
+                    d.x = uint16_t(it->second >> 16);
+                } else if (d.op == D_STR) {
+                    for (auto& [cc, i] : consumers[d.imm]) {
+                        DIns x{};
+                        x.op = D_STX;
+                        x.w = d.w;
+                        x.a = d.a;
+                        x.c = uint16_t(cc % C);
+                        x.b = uint16_t(i & 0xffff);
+                        x.x = uint16_t(i >> 16);
+                        x.imm = d.imm;
+                        stx.push_back(x);
+                    }
+                }
+            }
+        for (size_t k = 0; k < stx.size(); k += 32) {
+            Step st;
+            st.flags = kStepGeneric;
+            st.ins.assign(stx.begin() + k, stx.begin() + std::min(stx.size(), k + 32));
+            steps[p].push_back(std::move(st));
+        }
+    }
+
+    // rebuild the bundle rows and the compact programs
+    low.s_ins.clear();
+    low.c_words.clear();
+    low.max_bundles = 0;
+    for (size_t p = 0; p < NP; p++) {
+        const uint32_t nb = uint32_t(steps[p].size()), tw = (nb + 3) & ~3u;
+        low.s_off[p] = uint32_t(low.s_ins.size() / 32);
+        low.s_len[p] = nb;
+        low.max_bundles = std::max(low.max_bundles, nb);
+        low.c_off[p] = uint32_t(low.c_words.size());
+        std::vector<uint32_t> prog(tw, 0);
+        uint32_t first = 0;
+        for (uint32_t b = 0; b < nb; b++) {
+            const auto& st = steps[p][b];
+            const size_t base = low.s_ins.size();
+            low.s_ins.resize(base + 32, DIns{});
+            std::copy(st.ins.begin(), st.ins.end(), low.s_ins.begin() + base);
+            prog[b] = first | (uint32_t(st.ins.size()) << 16) | st.flags;
+            for (const DIns& d : st.ins) {
+                uint32_t w4[4];
+                memcpy(w4, &d, 16);
+                prog.insert(prog.end(), w4, w4 + 4);
+            }
+            first += uint32_t(st.ins.size());
+        }
+        if (first > 0xffff) { err = "process has too many instructions for one program"; return SIM_ERR_CAPACITY; }
+        low.c_size[p] = uint32_t(prog.size());
+        low.c_words.insert(low.c_words.end(), prog.begin(), prog.end());
+    }
+    return SIM_OK;
+}
+
 }  // namespace rtl

@@ -112,6 +112,27 @@ struct Lowered {
 
 int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& err);
 
+// Cluster exchange.  Processes are placed on a grid of thread-block
+// clusters (C CTAs of W warps, one process per warp) so that producers and
+// consumers of register values share a cluster where the greedy placement
+// can arrange it.  Each CTA keeps a double-buffered mirror of the registers
+// its processes read from producers inside the cluster: such reads become
+// D_LDM (from the mirror) and each producer appends D_STX instructions that
+// write the next value into the mirror of every consuming CTA of its cluster
+// (distributed shared memory); reads across clusters stay D_LDR (HBM/L2).
+struct ClusterPlan {
+    uint32_t C = 0, W = 0, grid = 0;
+    std::vector<uint32_t> warp_proc;   // process of each warp (grid * W), kNoProc if idle
+    std::vector<uint32_t> mir_off;     // per CTA: first mirror entry (grid + 1 offsets)
+    std::vector<uint32_t> mir_reg;     // register held by each mirror entry
+    uint32_t mirror_words = 0;         // largest per-CTA mirror (entries per buffer)
+    uint64_t reads_local = 0;          // cross-process register reads inside a cluster
+    uint64_t reads_remote = 0;         // ... and across clusters
+};
+// Rewrites the LANE_OP tables of `low` (bundles and compact programs).
+int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_t W, Lowered& low, ClusterPlan& plan,
+                   std::string& err);
+
 // register index -> (class, index in class)
 struct RegLayout {
     std::vector<uint8_t> cls;

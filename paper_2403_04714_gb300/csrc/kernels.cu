@@ -147,6 +147,77 @@ __device__ void task_lane_inst(const DevProg& P, const DevState& S, uint32_t p, 
 }
 
 // ---------------------------------------------------------------------------
+// Thread-block-cluster primitives (distributed shared memory, sm_90+)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// Store into the same shared-memory offset of CTA `rank` of this cluster.
+__device__ __forceinline__ void st_peer_u64(uint32_t local_addr, uint32_t rank, uint64_t v) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(local_addr), "r"(rank));
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(ra), "l"(v) : "memory");
+}
+
+// Hardware cluster barrier (all threads of every CTA of the cluster); used
+// only where every thread is known to arrive: kernel entry and exit.
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_peer(uint64_t* bar, uint32_t rank) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_addr(bar)), "r"(rank));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(ra) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Per-cycle barrier of a grid that is one cluster (bounded like the grid
+// barrier).  Each CTA arrives once on the barrier of every CTA of the cluster
+// (release at cluster scope: its stores of the cycle, into peers' mirrors and
+// global memory, become visible to whoever completes the phase) and then
+// waits on its own.  Cycles alternate between two barriers so that an early
+// arrival for cycle c+1 can never complete the phase of cycle c.
+static __device__ bool cluster_barrier(uint64_t* bars, uint32_t c, uint32_t C, uint64_t timeout_ns, int32_t* err,
+                                       bool skip, uint64_t* rec = nullptr) {
+    __shared__ int s_ok;
+    uint64_t* bar = bars + (c & 1);
+    __syncthreads();
+    if (threadIdx.x == 0 && rec) rec[0] = globaltimer_ns();
+    if (threadIdx.x < C && !skip) mbar_arrive_peer(bar, threadIdx.x);
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const uint64_t start = globaltimer_ns();
+        while (!mbar_try_wait(bar, (c >> 1) & 1)) {
+            if (ld_volatile(err) != 0) { ok = 0; break; }
+            if (globaltimer_ns() - start > timeout_ns) {
+                atomicCAS(err, 0, (int32_t)SIM_ERR_TIMEOUT);
+                ok = 0;
+                break;
+            }
+        }
+        if (rec) rec[1] = globaltimer_ns();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
 // LANE_OP: one warp, one process, one instance; lanes run a 32-wide step.
 // ---------------------------------------------------------------------------
 // All 13 operators without branches: every candidate result is formed and the
@@ -174,7 +245,8 @@ __device__ __forceinline__ uint64_t alu_select(uint32_t op, uint64_t a, uint64_t
 template <bool DIGEST>
 __device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, const DevState& S, uint32_t inst, uint64_t t,
                                              uint64_t key, int32_t col, bool pending, uint64_t* __restrict__ sl,
-                                             uint64_t& dacc) {
+                                             uint64_t& dacc, const uint64_t* mir_cur = nullptr,
+                                             uint32_t mir_nxt = 0) {
     const uint32_t par = uint32_t(t & 1), nxt = par ^ 1;
     if (d.op >= D_ADD && d.op <= D_CONCAT) {
         sl[d.dst] = alu_select(d.op, sl[d.a], sl[d.b], sl[d.c], d.x) & wmask(d.w);
@@ -221,11 +293,14 @@ __device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, con
             if (DIGEST) mem_digest_update(S, d.imm, inst, t, delta);
         }
         break;
-    case D_MUX:
-        sl[d.dst] = alu(D_MUX, sl[d.a], sl[d.b], sl[d.c], 0) & wmask(d.w);
+    case D_LDM:   // mirror entry (cluster exchange): this cycle's value of a register
+        sl[d.dst] = mir_cur[d.b | (d.x << 16)];
+        break;
+    case D_STX:   // next value into the mirror of cluster CTA d.c
+        st_peer_u64(mir_nxt + 8u * (d.b | (d.x << 16)), d.c, sl[d.a] & wmask(d.w));
         break;
     default:
-        sl[d.dst] = alu(d.op, sl[d.a], sl[d.b], 0, d.x) & wmask(d.w);
+        break;
     }
 }
 
@@ -267,7 +342,8 @@ __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, ui
 template <bool DIGEST>
 __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t,
                                  bool pending, uint64_t* __restrict__ sl, const uint32_t* __restrict__ prog,
-                                 uint32_t lane, uint32_t dummy) {
+                                 uint32_t lane, uint32_t dummy, const uint64_t* mir_cur = nullptr,
+                                 uint32_t mir_nxt = 0) {
     const uint64_t key = S.key[inst];
     const int32_t col = DIGEST ? S.track[inst] : -1;
     uint64_t dacc = 0;
@@ -278,7 +354,9 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
         const uint32_t e_next = b + 1 < nb ? prog[b + 1] : 0;
         const uint32_t first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
         if (e & kStepGeneric) {
-            if (lane < cnt) exec_lane_op<DIGEST>(decode(ins[first + lane]), P, S, inst, t, key, col, pending, sl, dacc);
+            if (lane < cnt)
+                exec_lane_op<DIGEST>(decode(ins[first + lane]), P, S, inst, t, key, col, pending, sl, dacc, mir_cur,
+                                     mir_nxt);
         } else {
             const bool on = lane < cnt;
             const Dec d = decode(ins[on ? first + lane : first]);
@@ -340,6 +418,69 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
         }
     }
     if (A.grid_sync && A.n > 0)
+        final_commit(P, S, t_base + A.n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+}
+
+// Cluster exchange (LANE_OP, resident programs, one instance): warp w runs
+// process warp_proc[w]; each CTA keeps a double-buffered mirror of the
+// registers its processes read from producers in its cluster, which the
+// producers write with D_STX straight into the consumer's shared memory.
+// Mirror buffer t&1 holds cycle t's values; at launch it is filled from the
+// global state, which producers keep writing for readers in other clusters,
+// for the host and for the next launch.
+template <bool DIGEST>
+__global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, LaunchArgs A) {
+    extern __shared__ __align__(16) uint64_t smem[];
+    __shared__ __align__(8) uint64_t cbar[2];
+    const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const uint32_t warp = blockIdx.x * A.warps_per_cta + wib;
+    const uint64_t region = (uint64_t)A.slot_words + A.prog_words / 2;
+    uint64_t* sl = smem + (uint64_t)wib * region;
+    uint32_t* prog = reinterpret_cast<uint32_t*>(sl + A.slot_words);
+    uint64_t* mirror = smem + (uint64_t)A.warps_per_cta * region;
+    const uint32_t p = P.warp_proc[warp];
+    if (p != kNoProc) {
+        const uint4* src = reinterpret_cast<const uint4*>(P.c_words + P.c_off[p]);
+        uint4* dst = reinterpret_cast<uint4*>(prog);
+        for (uint32_t k = lane; k < P.c_size[p] / 4; k += 32) dst[k] = __ldg(src + k);
+        __syncwarp();
+    }
+    const uint64_t t_base = A.t0_dev ? *A.t0_dev + A.t0 : A.t0;
+    {
+        const uint32_t par = uint32_t(t_base & 1);
+        const uint32_t lo = P.mir_off[blockIdx.x], hi = P.mir_off[blockIdx.x + 1];
+        for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+            const uint32_t r = P.mir_reg[i];
+            mirror[(uint64_t)par * A.mirror_words + (i - lo)] = load_reg(S, par, P.reg_cls[r], P.reg_idx[r], 0);
+        }
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&cbar[0], A.cluster);
+        mbar_init(&cbar[1], A.cluster);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    cluster_sync_all();   // every CTA of the cluster runs; mirrors and barriers are ready
+    uint32_t gen = 0;
+    bool ok = true;
+    for (uint32_t c = 0; c < A.n && ok; c++) {
+        const uint64_t t = t_base + c;
+        const bool pending = c > 0 || A.pending_first;
+        uint64_t* rec = (A.phase && c < A.phase_n) ? A.phase + ((uint64_t)c * gridDim.x + blockIdx.x) * 3 : nullptr;
+        if (rec && threadIdx.x == 0) rec[0] = globaltimer_ns();
+        if (p != kNoProc) {
+            const uint32_t par = uint32_t(t & 1);
+            task_lane_op_res<DIGEST>(P, S, p, 0, t, pending, sl, prog, lane, A.slot_words - 1,
+                                     mirror + (uint64_t)par * A.mirror_words,
+                                     smem_addr(mirror + (uint64_t)(par ^ 1) * A.mirror_words));
+        }
+        const bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
+        if (A.one_cluster)
+            ok = cluster_barrier(cbar, c, A.cluster, A.timeout_ns, S.err, skip, rec ? rec + 1 : nullptr);
+        else
+            ok = grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip, rec ? rec + 1 : nullptr);
+    }
+    cluster_sync_all();   // no CTA exits while a peer may still write into its shared memory
+    if (ok && A.n > 0)
         final_commit(P, S, t_base + A.n, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
@@ -456,6 +597,79 @@ cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int
     void* args[] = {&p, &s, &a};
     if (cooperative) return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(threads), args, smem, st);
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
+}
+
+static void* cycles_cl_fn(bool digest) {
+    return digest ? reinterpret_cast<void*>(&k_cycles_cl<true>) : reinterpret_cast<void*>(&k_cycles_cl<false>);
+}
+
+// Shared-memory limit (monotonic, as for k_cycles) and, above the portable
+// cluster size of 8, the non-portable cluster size opt-in.
+cudaError_t prepare_cluster_kernel(size_t smem, uint32_t C) {
+    static std::mutex mu;
+    static size_t set_to[2] = {0, 0};
+    static bool nonportable[2] = {false, false};
+    std::lock_guard<std::mutex> g(mu);
+    for (int d = 0; d < 2; d++) {
+        if (smem > set_to[d]) {
+            cudaError_t e = cudaFuncSetAttribute(cycles_cl_fn(d), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+            set_to[d] = smem;
+        }
+        if (C > 8 && !nonportable[d]) {
+            cudaError_t e = cudaFuncSetAttribute(cycles_cl_fn(d), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+            nonportable[d] = true;
+        }
+    }
+    return cudaSuccess;
+}
+
+static cudaLaunchConfig_t cluster_config(int grid, int threads, size_t smem, uint32_t C, cudaStream_t st,
+                                         cudaLaunchAttribute* at, bool cooperative) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeCooperative;
+    at[1].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = cooperative ? 2 : 1;
+    return cfg;
+}
+
+// Clusters of C CTAs that can be resident at once.
+cudaError_t occupancy_clusters(int grid, int threads, size_t smem, uint32_t C, int* n_clusters) {
+    cudaLaunchAttribute at[2];
+    cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, nullptr, at, false);
+    return cudaOccupancyMaxActiveClusters(n_clusters, cycles_cl_fn(false), &cfg);
+}
+
+// A grid of several clusters synchronises with the grid barrier, so all of
+// them must be resident: cooperative launch when the driver accepts it with
+// clusters, else a plain cluster launch (the planner checked residency and
+// the barrier's wait is bounded either way).
+cudaError_t launch_cycles_cl(bool digest, int grid, int threads, size_t smem, uint32_t C, cudaStream_t st,
+                             const DevProg& P, const DevState& S, const LaunchArgs& A) {
+    DevProg p = P;
+    DevState s = S;
+    LaunchArgs a = A;
+    void* args[] = {&p, &s, &a};
+    cudaLaunchAttribute at[2];
+    const bool coop = grid > int(C);
+    cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, st, at, coop);
+    cudaError_t e = cudaLaunchKernelExC(&cfg, cycles_cl_fn(digest), args);
+    if (e != cudaSuccess && coop) {
+        cudaGetLastError();
+        cfg = cluster_config(grid, threads, smem, C, st, at, false);
+        e = cudaLaunchKernelExC(&cfg, cycles_cl_fn(digest), args);
+    }
+    return e;
 }
 
 cudaError_t launch_commit(int grid, cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t_end,

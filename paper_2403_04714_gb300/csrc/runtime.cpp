@@ -24,6 +24,10 @@ cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int
                           const DevProg& P, const DevState& S, const LaunchArgs& A);
 cudaError_t launch_commit(int grid, cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t_end,
                           const uint64_t* t0_dev);
+cudaError_t prepare_cluster_kernel(size_t smem, uint32_t C);
+cudaError_t occupancy_clusters(int grid, int threads, size_t smem, uint32_t C, int* n_clusters);
+cudaError_t launch_cycles_cl(bool digest, int grid, int threads, size_t smem, uint32_t C, cudaStream_t st,
+                             const DevProg& P, const DevState& S, const LaunchArgs& A);
 cudaError_t launch_advance(cudaStream_t st, uint64_t* t0_dev, uint64_t n);
 cudaError_t launch_state_digest(cudaStream_t st, const DevProg& P, const DevState& S, uint32_t par,
                                 const uint64_t* mem_word_off, uint64_t mem_words, uint64_t* out, uint32_t n_inst);
@@ -63,6 +67,23 @@ int sm_count() {
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
         return 152;
+    }
+    return n;
+}
+
+// Shared memory a cluster CTA requests at least: more than half an SM's,
+// so that no SM holds two CTAs of the grid (a doubly loaded SM would be the
+// straggler of every cycle).
+constexpr size_t kClusterCtaSmemMin = 116 * 1024;
+
+// Clusters of C CTAs (one per SM) that can be resident at once; without a
+// GPU (compile-only use) an even share of the SMs.
+int resident_clusters(uint32_t C, uint32_t W) {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || prepare_cluster_kernel(kClusterCtaSmemMin, C) != cudaSuccess ||
+        occupancy_clusters(int(C) * 64, int(W) * 32, kClusterCtaSmemMin, C, &n) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return std::max(1, sm_count() / int(C));
     }
     return n;
 }
@@ -112,6 +133,7 @@ struct sim_netlist {
     Netlist nl;
     Partition part;
     Lowered low;
+    ClusterPlan cplan;                    // cluster exchange placement (cfg.cluster_size > 0)
     RegLayout layout;
     sim_netlist_info info{};
     std::vector<uint32_t> mport_off, mport_id;
@@ -133,7 +155,8 @@ struct sim_batch {
     uint64_t seed = 0, cycle = 0;
     // program tables
     DBuf s_ins, s_off, s_len, c_words, c_off, c_size, b_ins, b_off, b_len, mport_off, mport_id, mem_lg, mem_w, mem_base,
-        in_w, reg_cls, reg_idx, mem_word_off;
+        in_w, reg_cls, reg_idx, mem_word_off, warp_proc, mir_off, mir_reg;
+    bool cluster = false;                   // cluster exchange kernel (k_cycles_cl)
     // state
     DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, rom_dig, bar, err, t0_dev,
         scratch, P_dev, S_dev, phase;
@@ -220,13 +243,30 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
         pc.random_seed = h->cfg.seed_partition;
         uint32_t target = h->cfg.target_processes;
         // defaults measured on GB300: one process per warp of 8-warp CTAs for a
-        // single instance; four processes per SM with lane = instance
+        // single instance; four processes per SM with lane = instance; with
+        // cluster exchange one process per warp of every resident cluster CTA
+        if (!target && h->cfg.cluster_size >= 2 && h->cfg.cluster_size <= 16) {
+            const uint32_t W = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
+            target = uint32_t(resident_clusters(h->cfg.cluster_size, W)) * h->cfg.cluster_size * W;
+        }
         if (!target) target = uint32_t(sm_count()) * (h->cfg.mode == SIM_MODE_LANE_INST ? 4 : 8);
         pc.target = target;
         rc = partition(h->nl, pc, h->part, err);
         if (rc) return set_err(rc, err);
         rc = lower(h->nl, h->part, h->low, err);
         if (rc) return set_err(rc, err);
+        if (h->cfg.cluster_size) {
+            const uint32_t C = h->cfg.cluster_size;
+            if (C < 2 || C > 16) return set_err(SIM_ERR_BADARG, "cluster_size must be 0 or 2..16");
+            if (h->cfg.mode == SIM_MODE_LANE_INST || h->cfg.lowering == SIM_LOWER_GENERATED)
+                return set_err(SIM_ERR_BADARG, "cluster exchange runs the per-operation bytecode (LANE_OP)");
+            if (h->cfg.kernel != SIM_KERNEL_PERSISTENT)
+                return set_err(SIM_ERR_BADARG, "cluster exchange runs the persistent kernel");
+            const uint32_t W = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
+            if (W > 32) return set_err(SIM_ERR_BADARG, "warps_per_cta above 32");
+            rc = lower_clusters(h->nl, h->part, C, W, h->low, h->cplan, err);
+            if (rc) return set_err(rc, err);
+        }
         h->layout = reg_layout(h->nl);
         const Netlist& nl = h->nl;
         h->mport_off.assign(1, 0);
@@ -320,6 +360,15 @@ int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* b
     case 14: pick(L.c_words); break;
     case 15: pick(L.c_off); break;
     case 16: pick(L.c_size); break;
+    case 17: pick(nl->cplan.warp_proc); break;
+    case 18: pick(nl->cplan.mir_off); break;
+    case 19: pick(nl->cplan.mir_reg); break;
+    case 20: {
+        const ClusterPlan& cp = nl->cplan;
+        if (cp.C) u64 = {cp.C, cp.W, cp.grid, cp.mirror_words, cp.reads_local, cp.reads_remote};
+        pick(u64);
+        break;
+    }
     default: return set_err(SIM_ERR_BADARG, "unknown table");
     }
     if (out) memcpy(out, src, std::min(n, *bytes));
@@ -410,6 +459,8 @@ int sync_state_view(sim_batch* b) {
 }
 
 cudaError_t launch_any(sim_batch* b, bool cooperative, int grid, const LaunchArgs& A) {
+    if (b->cluster)
+        return launch_cycles_cl(b->S.ring_cap > 0, grid, b->threads, b->smem, b->nl->cplan.C, b->stream, b->P, b->S, A);
     if (!b->generated)
         return launch_cycles(b->mode, b->S.ring_cap > 0, cooperative, grid, b->threads, b->smem, b->stream, b->P, b->S, A);
     const void* f = b->gen_kernel[b->S.ring_cap > 0 ? 1 : 0];
@@ -429,6 +480,37 @@ uint32_t resident_words(const Lowered& L, uint32_t total_warps) {
     uint64_t mx = 0;
     for (uint64_t v : per) mx = std::max(mx, v);
     return uint32_t(std::min<uint64_t>(mx, 0xffffffffu));
+}
+
+// Cluster exchange: one process per warp on the planned grid of clusters;
+// slots, resident program and the two mirror buffers in shared memory.
+int plan_launch_cluster(sim_batch* b) {
+    const Lowered& L = b->nl->low;
+    const ClusterPlan& cp = b->nl->cplan;
+    const size_t smem_cap = 220 * 1024;
+    b->warps = int(cp.W);
+    b->threads = int(cp.W) * 32;
+    b->grid = int(cp.grid);
+    b->max_grid = b->grid;
+    b->n_tasks = uint32_t(b->nl->part.procs.size());
+    b->slot_words = (L.max_s_slots + 2) & ~1u;
+    uint32_t pw = 0;
+    for (uint32_t p : cp.warp_proc)
+        if (p != kNoProc) pw = std::max(pw, L.c_size[p]);
+    b->prog_words = (pw + 3) & ~3u;
+    b->smem = size_t(cp.W) * (size_t(b->slot_words) * 8 + size_t(b->prog_words) * 4) + size_t(cp.mirror_words) * 16;
+    b->smem = std::max(b->smem, kClusterCtaSmemMin);
+    if (b->smem > smem_cap)
+        return set_err(SIM_ERR_CAPACITY, "cluster CTA needs " + std::to_string(b->smem) +
+                                             " bytes of shared memory (limit " + std::to_string(smem_cap) + ")");
+    CUDA_TRY(prepare_cluster_kernel(b->smem, cp.C));
+    int n_clusters = 0;
+    CUDA_TRY(occupancy_clusters(b->grid, b->threads, b->smem, cp.C, &n_clusters));
+    if (uint64_t(n_clusters) * cp.C < uint64_t(b->grid))
+        return set_err(SIM_ERR_CAPACITY, std::to_string(cp.grid / cp.C) + " clusters of " + std::to_string(cp.C) +
+                                             " CTAs requested, " + std::to_string(n_clusters) + " can be resident");
+    b->cluster = true;
+    return SIM_OK;
 }
 
 // Choose warps per CTA and grid for a batch (both lane mappings).  LANE_OP
@@ -503,7 +585,8 @@ int upload_program(sim_batch* b) {
         (rc = upload(b->mem_lg, nl.mem_lg, st)) || (rc = upload(b->mem_w, nl.mem_w, st)) ||
         (rc = upload(b->mem_base, mem_base, st)) || (rc = upload(b->in_w, nl.in_w, st)) ||
         (rc = upload(b->reg_cls, h->layout.cls, st)) || (rc = upload(b->reg_idx, h->layout.idx, st)) ||
-        (rc = upload(b->mem_word_off, h->mem_word_off, st)))
+        (rc = upload(b->mem_word_off, h->mem_word_off, st)) || (rc = upload(b->warp_proc, h->cplan.warp_proc, st)) ||
+        (rc = upload(b->mir_off, h->cplan.mir_off, st)) || (rc = upload(b->mir_reg, h->cplan.mir_reg, st)))
         return rc;
     DevProg& P = b->P;
     P.s_ins = b->s_ins.as<DIns>();
@@ -523,6 +606,9 @@ int upload_program(sim_batch* b) {
     P.in_w = b->in_w.as<uint8_t>();
     P.reg_cls = b->reg_cls.as<uint8_t>();
     P.reg_idx = b->reg_idx.as<uint32_t>();
+    P.warp_proc = b->warp_proc.as<uint32_t>();
+    P.mir_off = b->mir_off.as<uint32_t>();
+    P.mir_reg = b->mir_reg.as<uint32_t>();
     P.n_proc = uint32_t(h->part.procs.size());
     P.n_in = uint32_t(nl.in_w.size());
     P.n_reg = uint32_t(nl.reg_w.size());
@@ -694,6 +780,11 @@ LaunchArgs base_args(sim_batch* b) {
     A.proc_major = b->proc_major;
     A.wave_groups = b->wave_groups;
     A.cta_major = b->cta_major;
+    if (b->cluster) {
+        A.cluster = b->nl->cplan.C;
+        A.mirror_words = b->nl->cplan.mirror_words;
+        A.one_cluster = uint32_t(b->grid) == b->nl->cplan.C;
+    }
     return A;
 }
 
@@ -898,8 +989,12 @@ int sim_create_instances(sim_netlist* nl, uint32_t n_inst, uint64_t seed, void* 
         b->wave_groups = nl->cfg.wave_groups;
         b->cta_major = nl->cfg.task_order == SIM_ORDER_CTA_MAJOR;
         int rc;
+        if (nl->cfg.cluster_size && (n_inst != 1 || b->mode != SIM_MODE_LANE_OP))
+            return set_err(SIM_ERR_BADARG, "a netlist lowered for cluster exchange runs one instance (LANE_OP)");
         if ((rc = upload_program(b.get())) || (rc = init_state(b.get()))) return rc;
-        if (nl->cfg.lowering == SIM_LOWER_GENERATED) {
+        if (nl->cfg.cluster_size) {
+            if ((rc = plan_launch_cluster(b.get()))) return rc;
+        } else if (nl->cfg.lowering == SIM_LOWER_GENERATED) {
             if ((rc = ensure_loaded(nl, b->mode))) return rc;
             b->generated = true;
             b->gen_kernel[0] = reinterpret_cast<const void*>(nl->gen[b->mode].kernel[0]);

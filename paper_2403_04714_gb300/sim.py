@@ -46,7 +46,7 @@ class sim_config(C.Structure):
         ("digest_capacity", C.c_uint32), ("timeout_ms", C.c_uint32), ("big_array_bytes", C.c_uint64),
         ("disable_stage3", C.c_uint32), ("seed_partition", C.c_uint32), ("lowering", C.c_uint32),
         ("task_order", C.c_uint32), ("phase_samples", C.c_uint32), ("wave_groups", C.c_uint32),
-        ("reserved", C.c_uint32 * 4),
+        ("cluster_size", C.c_uint32), ("reserved", C.c_uint32 * 3),
     ]
 
 
@@ -128,7 +128,8 @@ TABLES = {"s_ins": (0, None), "s_off": (1, np.uint32), "s_len": (2, np.uint32), 
           "fiber_sink": (7, np.int32), "fiber_cost": (8, np.uint64), "proc_cost": (9, np.uint64),
           "reg_cls": (10, np.uint8), "reg_idx": (11, np.uint32), "s_slots": (12, np.uint32),
           "b_slots": (13, np.uint32), "c_words": (14, np.uint32), "c_off": (15, np.uint32),
-          "c_size": (16, np.uint32)}
+          "c_size": (16, np.uint32), "warp_proc": (17, np.uint32), "mir_off": (18, np.uint32),
+          "mir_reg": (19, np.uint32), "cluster_plan": (20, np.uint64)}
 # one 16-byte instruction of the device bytecode
 DINS = np.dtype([("op", np.uint8), ("w", np.uint8), ("dst", np.uint16), ("a", np.uint16), ("b", np.uint16),
                  ("c", np.uint16), ("x", np.uint16), ("imm", np.uint32)])

@@ -10,7 +10,7 @@ import oracle
 
 D_NOP, D_LDR, D_LDI, D_CONST, D_MEMRD = 0, 1, 2, 3, 4
 D_ADD, D_SUB, D_MUL, D_AND, D_OR, D_XOR, D_SHL, D_SHR, D_EQ, D_LT = range(5, 15)
-D_MUX, D_SLICE, D_CONCAT, D_STR, D_WREC, D_COMMIT = range(15, 21)
+D_MUX, D_SLICE, D_CONCAT, D_STR, D_WREC, D_COMMIT, D_LDM, D_STX = range(15, 23)
 M64 = (1 << 64) - 1
 
 
@@ -24,6 +24,15 @@ class Emu:
         self.py = PyNet(net_text)
         self.mode = mode
         self.seed, self.inst = seed, inst
+        self.cluster = None
+        if mode == "lane_op_cluster":
+            # cluster exchange: per-CTA mirrors written by D_STX, read by D_LDM
+            C, W, grid = (int(v) for v in netlist.table("cluster_plan")[:3])
+            warp_proc = netlist.table("warp_proc")
+            mir_off, mir_reg = netlist.table("mir_off"), netlist.table("mir_reg")
+            cta = {int(pr): w // W for w, pr in enumerate(warp_proc) if pr != 0xFFFFFFFF}
+            self.cluster = dict(C=C, cta=cta, mir_off=[int(v) for v in mir_off], mir_reg=[int(v) for v in mir_reg])
+            mode = "lane_op_compact"
         if mode == "lane_op_compact":
             # rebuild 32-wide rows from the shared-memory program format
             words = netlist.table("c_words")
@@ -60,6 +69,10 @@ class Emu:
             self.nslots = netlist.table("b_slots")
         self.mode = mode
         self.regs, self.mems = self.py.initial_state()
+        if self.cluster:
+            cl = self.cluster
+            cl["cur"] = [[self.regs[r] for r in cl["mir_reg"][cl["mir_off"][c]:cl["mir_off"][c + 1]]]
+                         for c in range(len(cl["mir_off"]) - 1)]
         self.cycle = 0
         self.pending = {}           # port -> (en, addr, data) of the previous cycle
         self.n_in = len(self.py.inputs)
@@ -108,6 +121,22 @@ class Emu:
             if self.pending:
                 self._commit(int(d["imm"]))
             return None
+        if op == D_LDM:
+            cl = self.cluster
+            c = cl["cta"][self.proc]
+            i = int(d["b"]) | (int(d["x"]) << 16)
+            assert cl["mir_reg"][cl["mir_off"][c] + i] == int(d["imm"]), "mirror entry holds another register"
+            v = cl["cur"][c][i]
+            assert v == self.regs[int(d["imm"])], "stale mirror value"
+            return v
+        if op == D_STX:
+            cl = self.cluster
+            c = cl["cta"][self.proc] // cl["C"] * cl["C"] + int(d["c"])
+            i = int(d["b"]) | (int(d["x"]) << 16)
+            assert cl["mir_reg"][cl["mir_off"][c] + i] == int(d["imm"]), "mirror write to the wrong entry"
+            assert cl["nxt"][c][i] is None, "mirror entry written twice"
+            cl["nxt"][c][i] = S("a") & mask(w)
+            return None
         a, b = S("a"), S("b")
         if op == D_MUX:
             v = b if a != 0 else S("c")
@@ -128,7 +157,10 @@ class Emu:
         nxt = [None] * len(self.regs)
         recs = {}
         procs = order if order is not None else range(len(self.off))
+        if self.cluster:
+            self.cluster["nxt"] = [[None] * len(v) for v in self.cluster["cur"]]
         for p in procs:
+            self.proc = p
             slots = [None] * int(self.nslots[p])
             if self.mode == "lane_op":
                 for b in range(int(self.len[p])):
@@ -145,6 +177,10 @@ class Emu:
                     if v is not None:
                         slots[int(d["dst"])] = v
         assert all(v is not None for v in nxt), "a register got no next value"
+        if self.cluster:
+            for c, v in enumerate(self.cluster["nxt"]):
+                assert all(x is not None for x in v), f"mirror of CTA {c} not fully written"
+            self.cluster["cur"] = self.cluster["nxt"]
         self.regs = nxt
         self.pending = recs
         self.cycle += 1

@@ -12,8 +12,12 @@ from paper_2403_04714_gb300 import netgen, sim
 from test_oracle_bruteforce import random_tiny_circuit
 
 
-def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False):
-    nl = sim.Netlist(text, mode=mode.replace("_compact", ""), target_processes=target, seed_partition=seed_partition)
+def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False, cluster=None):
+    extra = {}
+    if cluster:
+        extra = dict(cluster_size=cluster[0], warps_per_cta=cluster[1])
+    base_mode = mode.replace("_compact", "").replace("_cluster", "")
+    nl = sim.Netlist(text, mode=base_mode, target_processes=target, seed_partition=seed_partition, **extra)
     emu = Emu(text, nl, mode, seed=42, inst=0)
     ref = oracle.Sim(oracle.Net(text=text), seed=42, inst=0)
     rng = random.Random(1)
@@ -49,3 +53,26 @@ def test_flat_netlist_with_rams(mode):
     text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
     for target, sp in ((16, 0), (40, 3)):
         run_compare(text, mode, 30, target=target, seed_partition=sp, shuffle=True)
+
+
+# Cluster exchange: reads from producers in the same cluster come from the
+# CTA's mirror (D_LDM), which the producers write with D_STX; the emulator
+# checks every mirror read against the register and every mirror entry for
+# exactly one write per cycle.
+@pytest.mark.parametrize("C,W,target", [(2, 2, 8), (2, 1, 5), (4, 2, 16)])
+def test_cluster_tiny(C, W, target):
+    text = open(netgen.cached_netlist("tiny")).read()
+    run_compare(text, "lane_op_cluster", 30, target=target, shuffle=True, cluster=(C, W))
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_cluster_random_circuits_with_memory(seed):
+    text = random_tiny_circuit(seed).to_text()
+    for C, W, target in ((2, 1, 2), (2, 1, 4), (4, 1, 4), (2, 2, 3)):
+        run_compare(text, "lane_op_cluster", 20, target=target, shuffle=True, cluster=(C, W))
+
+
+def test_cluster_flat_netlist_with_rams():
+    text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
+    for C, W, target in ((4, 2, 16), (4, 2, 8), (8, 4, 40)):
+        run_compare(text, "lane_op_cluster", 20, target=target, shuffle=True, cluster=(C, W))
