@@ -2,7 +2,8 @@
 
 Headline workload: the mid netlist (200k ops, 20k registers: 30% 1-bit,
 40% 32-bit, 30% 64-bit, depth 60, two 512x64-bit synchronous RAMs), one
-instance, 100,000 simulated cycles, persistent kernel with a grid barrier.
+instance, 100,000 simulated cycles, persistent kernel; partition size, warps
+per CTA and thread-block-cluster exchange picked by the autotuner.
 A step is one sim_step of `--cycles` simulated cycles (default 10,000), so
 the default 10 timed steps simulate the full 100k-cycle workload.
 
@@ -32,7 +33,7 @@ UNIT = "simulated cycles/s"
 STATE_BYTES_MID = 6126 / 8 + 7955 * 4 + 5927 * 8
 WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
             "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
-            "100k cycles; persistent kernel, grid barrier")
+            "100k cycles; persistent kernel, autotuned geometry (grid barrier, optional cluster exchange)")
 
 
 def peaks():
@@ -201,6 +202,42 @@ def prng_row(stream, per_proc=(1, 8, 64), procs=1216, cycles=2000):
     return out
 
 
+def cluster_row(stream, flush):
+    """Cluster exchange against the plain grid-barrier kernel, one instance: a
+    design that fits one 16-CTA cluster synchronises with the cluster barrier
+    and exchanges every value through distributed shared memory."""
+    from paper_2403_04714_gb300 import netgen, sim
+    import numpy as np
+    cases = {
+        "tiny": (open(netgen.cached_netlist("tiny"), "rb").read(), dict(), dict(cluster_size=8, warps_per_cta=2,
+                                                                              target_processes=16)),
+        "prng_1216_fibers": (netgen.gen_prng(1216).to_text(), dict(target_processes=1216),
+                             dict(cluster_size=16, warps_per_cta=8, target_processes=128)),
+        "mid": (open(netgen.cached_netlist("mid"), "rb").read(), dict(warps_per_cta=4, target_processes=576),
+                dict(cluster_size=4, warps_per_cta=4)),
+    }
+    out = {}
+    for name, (text, plain, clus) in cases.items():
+        r = {}
+        for kind, cfg in (("grid_barrier", plain), ("cluster", clus)):
+            nl = sim.Netlist(text, mode="lane_op", phase_samples=500, **cfg)
+            b = sim.Batch(nl, 1, seed=42, stream=stream)
+            cyc = 5000 if name != "mid" else 2000
+            ms, _ = time_steps(b, stream, 3, 1, cyc, flush)
+            b.step(500)
+            ph = np.median(b.phase_times(500)[50:], axis=0)
+            r[kind] = {"cycles_per_s": 3 * cyc / (sum(ms) / 1000.0), "compute_ns": float(ph[0]),
+                       "sync_ns": float(ph[1]), "processes": nl.info()["n_processes"],
+                       "ctas": b.launch_info()["ctas"], "config": cfg}
+            if kind == "cluster":
+                plan = nl.table("cluster_plan")
+                r[kind]["reads_in_cluster"] = int(plan[4])
+                r[kind]["reads_across_clusters"] = int(plan[5])
+            del b, nl
+        out[name] = r
+    return out
+
+
 def served_row(n_jobs=40):
     """Continuous batching over a seeded Poisson trace of jobs (p50/p99 latency)."""
     from paper_2403_04714_gb300 import netgen, sim
@@ -289,8 +326,8 @@ def main():
     ap.add_argument("--cpu-cycles", type=int, default=3000, help="oracle sample for cpu_baseline")
     ap.add_argument("--batched-cycles", type=int, default=200)
     ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
-    ap.add_argument("--rows", default="single,batched,mesh,served",
-                    help="comma list of extra rows: single, batched, mesh, served")
+    ap.add_argument("--rows", default="single,batched,mesh,cluster,served",
+                    help="comma list of extra rows: single, batched, mesh, cluster, served")
     args = ap.parse_args()
     rank, world, local, dist = (0, 1, 0, None)
     if args.impl == "reference":
@@ -315,8 +352,10 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
     p = peaks()
 
-    # ---- headline: single instance, persistent kernel --------------------------
-    nl = sim.Netlist(text, mode="lane_op")
+    # ---- headline: single instance, persistent kernel, autotuned geometry ------
+    from paper_2403_04714_gb300 import autotune
+    tuned = autotune.autotune(text, 1)
+    nl = sim.Netlist(text, kernel="persistent", **tuned["config"])
     info = nl.info()
     b = sim.Batch(nl, 1, seed=42 + rank, stream=stream)
     barrier(dist)
@@ -383,6 +422,8 @@ def main():
             rows["prng_sync"] = prng_row(stream)
         if "mesh" in want:
             rows["mesh_single"] = mesh_row(stream, flush)
+        if "cluster" in want:
+            rows["cluster_exchange"] = cluster_row(stream, flush)
         if "served" in want:
             rows["served"] = served_row()
 
@@ -402,10 +443,13 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "cycles_per_step": args.cycles, "instances": 1,
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
-                       "processes": info["n_processes"], "launch": geo},
+                       "processes": info["n_processes"], "launch": geo,
+                       "autotuned": {"config": tuned["config"], "cached": tuned["cached"],
+                                     "candidates": tuned["results"]}},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "k_cycles<LANE_OP> (persistent)",
+                         "kernel": "k_cycles_cl (cluster exchange)" if tuned["config"].get("cluster_size")
+                                   else "k_cycles<LANE_OP> (persistent)",
                          "note": "word ops (algorithmic, unduplicated) per second; peak = 152 SMs x 128 lanes "
                                  "x max SM clock; single-instance BSP is latency-bound"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),

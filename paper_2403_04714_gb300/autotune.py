@@ -2,7 +2,8 @@
 
 Candidates vary what the compiler cannot decide alone: the partition size
 (SLB target process count), warps per CTA (with lane = instance: instances
-per CTA = 32 x warps), the task order, and the lowering.  Each candidate is
+per CTA = 32 x warps), the task order, the lowering and, for one instance,
+the thread-block cluster size of the distributed-shared-memory exchange.  Each candidate is
 timed on a short run of the real workload with CUDA events; the best one is
 persisted in a JSON cache keyed by a hash of the netlist text, the instance
 count and the GPU name, so later runs reuse it without measuring.
@@ -23,12 +24,17 @@ def _key(text: bytes, n_inst: int, device: str) -> str:
     return hashlib.sha256(text + f"|{n_inst}|{device}".encode()).hexdigest()[:24]
 
 
-def default_candidates(n_inst: int):
+def default_candidates(n_inst: int, sms: int = 152):
     if n_inst >= 32:
         return [dict(mode="lane_inst", lowering="generated", warps_per_cta=w, task_order=o)
                 for w in (8, 4) for o in ("process_major", "group_major")]
-    return [dict(mode="lane_op", lowering="bytecode", warps_per_cta=w, target_processes=tp)
-            for w, tp in ((8, 0), (16, 2432), (4, 608))]
+    cands = [dict(mode="lane_op", lowering="bytecode"),                      # adaptive: 4 or 8 per SM
+             dict(mode="lane_op", lowering="bytecode", warps_per_cta=8, target_processes=8 * sms),
+             dict(mode="lane_op", lowering="bytecode", warps_per_cta=3, target_processes=3 * sms)]
+    if n_inst == 1:     # cluster exchange (one instance): several clusters, and one 16-CTA cluster
+        cands += [dict(mode="lane_op", lowering="bytecode", cluster_size=c, warps_per_cta=w)
+                  for c, w in ((4, 4), (2, 4), (16, 8))]
+    return cands
 
 
 def measure(text: bytes, n_inst: int, cfg: dict, cycles: int, seed: int = 1) -> float:
@@ -80,7 +86,10 @@ def autotune(text: bytes | str, n_inst: int, candidates=None, cycles: int | None
         out = dict(cache[key])
         out["cached"] = True
         return out
-    candidates = candidates or default_candidates(n_inst)
+    if candidates is None:
+        import torch
+        sms = torch.cuda.get_device_properties(0).multi_processor_count if torch.cuda.is_available() else 152
+        candidates = default_candidates(n_inst, sms)
     cycles = cycles or (50 if n_inst >= 32 else 2000)
     results = []
     t0 = time.time()

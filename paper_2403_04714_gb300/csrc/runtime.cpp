@@ -249,10 +249,21 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
             const uint32_t W = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
             target = uint32_t(resident_clusters(h->cfg.cluster_size, W)) * h->cfg.cluster_size * W;
         }
-        if (!target) target = uint32_t(sm_count()) * (h->cfg.mode == SIM_MODE_LANE_INST ? 4 : 8);
+        const bool adaptive = !target && h->cfg.mode != SIM_MODE_LANE_INST;
+        if (!target) target = uint32_t(sm_count()) * 4;
         pc.target = target;
         rc = partition(h->nl, pc, h->part, err);
         if (rc) return set_err(rc, err);
+        // one instance: four processes per SM unless merging that far leaves a
+        // straggler well above the slowest fiber (the t_comp bound of the
+        // partition); then eight.  Measured on GB300: the 200k-op netlist
+        // reaches its bound at four (fewer warps per SM, shorter steps), the
+        // 2M-op mesh keeps gaining up to eight.
+        if (adaptive && h->part.proc_cost_max * 4 > h->part.fiber_cost_max * 5) {
+            pc.target = uint32_t(sm_count()) * 8;
+            rc = partition(h->nl, pc, h->part, err);
+            if (rc) return set_err(rc, err);
+        }
         rc = lower(h->nl, h->part, h->low, err);
         if (rc) return set_err(rc, err);
         if (h->cfg.cluster_size) {
@@ -532,6 +543,8 @@ int plan_launch(sim_batch* b) {
         return set_err(SIM_ERR_CAPACITY, "a process needs " + std::to_string(slot_bytes) +
                                              " bytes of value slots per warp (limit " + std::to_string(smem_cap) + ")");
     int warps = b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8;
+    if (!b->nl->cfg.warps_per_cta && b->mode == SIM_MODE_LANE_OP)   // one process per warp, one CTA per SM
+        warps = int(std::min<uint64_t>(16, std::max<uint64_t>(1, (uint64_t(n_proc) * b->I + sms - 1) / sms)));
     while (warps > 1 && size_t(warps) * slot_bytes > smem_cap) warps /= 2;
     b->warps = warps;
     b->threads = warps * 32;
