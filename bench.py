@@ -31,6 +31,10 @@ METRIC = "simulated cycles/s (1 instance) and instance-cycles/s (batched), p50/p
 UNIT = "simulated cycles/s"
 # bytes of one instance's register state (1-bit packed, 32-bit and 64-bit planes)
 STATE_BYTES_MID = 6126 / 8 + 7955 * 4 + 5927 * 8
+# dram__bytes_read.sum + dram__bytes_write.sum of one 10,000-cycle launch of
+# the headline kernel (ncu, 1 pass): the one-time program and table load; the
+# per-cycle exchange stays in L2.  Command and figures: profiles/k_cycles_cl_mid_single.md
+HEADLINE_TRAFFIC = 4.84e6 + 0.103e6
 WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
             "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
             "100k cycles; persistent kernel, autotuned geometry (grid barrier, optional cluster exchange)")
@@ -447,7 +451,7 @@ def main():
                        "autotuned": {"config": tuned["config"], "cached": tuned["cached"],
                                      "candidates": tuned["results"]}},
             "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": HEADLINE_TRAFFIC,
                          "kernel": "k_cycles_cl (cluster exchange)" if tuned["config"].get("cluster_size")
                                    else "k_cycles<LANE_OP> (persistent)",
                          "note": "word ops (algorithmic, unduplicated) per second; peak = 152 SMs x 128 lanes "
