@@ -57,11 +57,13 @@ void write_file(const std::string& path, const std::vector<char>& data) {
 
 // Registers per thread for generated code.  Process functions with many live
 // values would otherwise claim up to 255 registers and hold one 256-thread
-// CTA per SM; at 64 the spills are few and four CTAs fit (measured on the
-// 200k-op netlist with 4096 instances: 3.6M -> 6.9M instance-cycles/s).
+// CTA per SM.  Measured on the 200k-op netlist with 4,096 instances (8-warp
+// CTAs): uncapped 3.6M instance-cycles/s; 64 registers (4 CTAs per SM) 6.9M;
+// 80 (3 CTAs) 7.5M; 96 and 128 (2 CTAs) 4.8-5.0M.  Spills fall from 1.9 GB
+// to 1.3 GB of local traffic per simulated cycle between 64 and 80.
 std::string max_registers() {
     const char* m = getenv("RTLSIM_GEN_MAXRREG");
-    return m ? m : "64";
+    return m ? m : "80";
 }
 
 int compile_unit(const GenUnit& u, std::vector<char>& cubin, std::string& err) {
@@ -76,6 +78,13 @@ int compile_unit(const GenUnit& u, std::vector<char>& cubin, std::string& err) {
     std::vector<const char*> opts = {arch.c_str(), "-rdc=true", "--std=c++17", "-default-device", "-w"};
     std::string maxr = "--maxrregcount=" + max_registers();
     opts.push_back(maxr.c_str());
+    // the kernel entry's launch bound must leave every process function its
+    // register cap: the largest power-of-two CTA with cap x threads <= 65536
+    const int cap = std::max(16, std::min(255, atoi(max_registers().c_str())));
+    int threads = 1024;
+    while (threads > 32 && threads * cap > 65536) threads /= 2;
+    std::string thr = "-DRTLSIM_GEN_MAX_THREADS=" + std::to_string(threads);
+    opts.push_back(thr.c_str());
     nvrtcResult r = nvrtcCompileProgram(prog, int(opts.size()), opts.data());
     if (r != NVRTC_SUCCESS) {
         size_t n = 0;

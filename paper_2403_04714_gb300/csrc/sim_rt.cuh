@@ -263,12 +263,18 @@ __device__ __forceinline__ void gen_cycles(const DevProg* __restrict__ Pg, const
 
 }  // namespace rtl
 
+// Threads per CTA the generated kernels are compiled for: 1024 at the default
+// 64-register cap; a higher cap (RTLSIM_GEN_MAXRREG) compiles for fewer.
+#ifndef RTLSIM_GEN_MAX_THREADS
+#define RTLSIM_GEN_MAX_THREADS 1024
+#endif
+
 #define RTLSIM_GEN_KERNELS(MODE)                                                                              \
-    extern "C" __global__ void __launch_bounds__(1024)                                                        \
+    extern "C" __global__ void __launch_bounds__(RTLSIM_GEN_MAX_THREADS)                                      \
         rtl_gen_d0(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
         rtl::gen_cycles<MODE, false>(P, S, A);                                                                \
     }                                                                                                         \
-    extern "C" __global__ void __launch_bounds__(1024)                                                        \
+    extern "C" __global__ void __launch_bounds__(RTLSIM_GEN_MAX_THREADS)                                      \
         rtl_gen_d1(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
         rtl::gen_cycles<MODE, true>(P, S, A);                                                                 \
     }
