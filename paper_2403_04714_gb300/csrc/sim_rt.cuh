@@ -29,20 +29,30 @@ __device__ __forceinline__ uint64_t globaltimer_ns() {
     return t;
 }
 
-__device__ __forceinline__ uint32_t ld_acquire(const uint32_t* p) {
-    uint32_t v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
 __device__ __forceinline__ int32_t ld_volatile(const int32_t* p) { return *(volatile const int32_t*)p; }
 
 
-// Grid-wide barrier: arrival counter plus generation word.  Every wait is
-// bounded: past `timeout_ns`, or once another CTA has recorded an error, the
-// CTA records SIM_ERR_TIMEOUT (first error wins) and returns false.
-// With `rec` set, thread 0 stores the time the whole CTA arrived (rec[0]) and
-// the time the barrier released it (rec[1]), from %globaltimer.
+__device__ __forceinline__ uint64_t ld_acquire_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Grid-wide barrier on one monotonic 64-bit arrival counter (zeroed before
+// each launch): barrier number g of the launch is complete once the counter
+// reaches (g+1) x gridDim.x.  Each CTA adds its arrival with a release
+// reduction (no round trip: the CTA's stores of the cycle, ordered before it
+// by __syncthreads, become visible to every CTA that acquires the count) and
+// then polls the counter with acquire loads; nobody has to reset a counter or
+// publish a generation word, so the last arrival releases everyone directly.
+// Every wait is bounded: past `timeout_ns`, or once another CTA has recorded
+// an error, the CTA records SIM_ERR_TIMEOUT (first error wins) and returns
+// false.  With `rec` set, thread 0 stores the time the whole CTA arrived
+// (rec[0]) and the time the barrier released it (rec[1]), from %globaltimer.
 static __device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeout_ns, int32_t* err, bool skip,
                                     uint64_t* rec = nullptr) {
     __shared__ int s_ok;
@@ -50,17 +60,11 @@ static __device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeo
     if (threadIdx.x == 0) {
         int ok = 1;
         if (rec) rec[0] = globaltimer_ns();
-        __threadfence();
-        if (!skip) {
-            uint32_t arrived = atomicAdd(&bar[0], 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(&bar[0], 0u);
-                __threadfence();
-                atomicExch(&bar[1], gen + 1);
-            }
-        }
-        uint64_t start = globaltimer_ns();
-        while (ld_acquire(&bar[1]) == gen) {
+        unsigned long long* count = reinterpret_cast<unsigned long long*>(bar);
+        const unsigned long long target = (unsigned long long)(gen + 1) * gridDim.x;
+        if (!skip) red_release_add(count, 1ull);
+        const uint64_t start = globaltimer_ns();
+        while (ld_acquire_u64(count) < target) {
             if (ld_volatile(err) != 0) { ok = 0; break; }
             if (globaltimer_ns() - start > timeout_ns) {
                 atomicCAS(err, 0, (int32_t)SIM_ERR_TIMEOUT);
@@ -69,7 +73,6 @@ static __device__ bool grid_barrier(uint32_t* bar, uint32_t& gen, uint64_t timeo
             }
         }
         gen++;
-        __threadfence();
         if (rec) rec[1] = globaltimer_ns();
         s_ok = ok;
     }
