@@ -134,6 +134,11 @@ class Sim:
     def cycle(self):
         return lib().orc_sim_cycle(self._h)
 
+    def set_cycle(self, c):
+        """Set the cycle counter (resuming from a state taken at cycle c: the
+        stimulus of cycle t depends on t)."""
+        lib().orc_sim_set_cycle(self._h, c)
+
     def digest(self):
         return lib().orc_sim_digest(self._h)
 
