@@ -50,10 +50,13 @@ def peaks():
         return {}
 
 
-# Integer issue peak (no measured integer peak exists): 152 SMs x 4 SM
-# sub-partitions x 32 lanes x 1 instruction/clock at the maximum SM clock.
+# Integer ALU peak (no measured integer peak in the driver's file): 152 SMs x
+# 4 sub-partitions x 16 lanes per clock of the integer ALU pipe (IADD3, LOP3,
+# SHF, ISETP, SEL: half a warp instruction per clock per sub-partition, as the
+# pipe utilisation ncu reports for the interpreter confirms) at the maximum SM
+# clock.  bench also reports sim_measure_int_peak beside it.
 def alu_peak_ops(p):
-    return 152 * 4 * 32 * float(p.get("sm_max_mhz", 2070.0)) * 1e6
+    return 152 * 4 * 16 * float(p.get("sm_max_mhz", 2070.0)) * 1e6
 
 
 class ClockSampler:
@@ -170,17 +173,20 @@ def mesh_row(stream, flush):
             "processes": i["n_processes"], "max_bundles": i["max_bundles"]}
 
 
-def phase_row(text, stream, cycles=500):
+def phase_row(text, stream, cycles=500, cfg=None):
     """Decomposition of a simulated cycle of the headline workload (Eq. sim_rate)."""
     from paper_2403_04714_gb300 import sim
     import numpy as np
-    nl = sim.Netlist(text, mode="lane_op", phase_samples=cycles)
+    cfg = dict(cfg or {"mode": "lane_op"})
+    nl = sim.Netlist(text, kernel="persistent", phase_samples=cycles, **cfg)
     b = sim.Batch(nl, 1, seed=42, stream=stream)
     b.step(cycles)
     b.step(cycles)
     ph = b.phase_times(cycles)[50:]          # skip the first cycles of the launch
     med = np.median(ph, axis=0)
+    steps = nl.info()["max_bundles"]
     return {"compute_ns": float(med[0]), "sync_ns": float(med[1]), "cycle_ns": float(med[2]),
+            "steps_slowest_process": steps, "ns_per_step": float(med[0]) / max(1, steps), "config": cfg,
             "note": "medians over cycles 50..500 of one persistent launch; compute = earliest CTA start "
                     "to last CTA arrival (straggler t_comp + t_comm), sync = last arrival to last release"}
 
@@ -424,7 +430,7 @@ def main():
             }
             del bb, nlb
         if "single" in want:
-            rows["phases"] = phase_row(text, stream)
+            rows["phases"] = phase_row(text, stream, cfg=tuned["config"])
             rows["prng_sync"] = prng_row(stream)
         if "mesh" in want:
             rows["mesh_single"] = mesh_row(stream, flush)
@@ -432,6 +438,9 @@ def main():
             rows["cluster_exchange"] = cluster_row(stream, flush)
         if "served" in want:
             rows["served"] = served_row()
+
+    # ---- measured integer issue rate (the ALU roof, next to the derived one) ---
+    int_peak = sim.measure_int_peak(1 << 14)
 
     # ---- CPU baseline: the oracle on one host core, bounded sample -------------
     cpu = None
@@ -456,8 +465,11 @@ def main():
                          "frac": achieved / peak, "traffic": HEADLINE_TRAFFIC,
                          "kernel": "k_cycles_cl (cluster exchange)" if tuned["config"].get("cluster_size")
                                    else "k_cycles<LANE_OP> (persistent)",
-                         "note": "word ops (algorithmic, unduplicated) per second; peak = 152 SMs x 128 lanes "
-                                 "x max SM clock; single-instance BSP is latency-bound"},
+                         "measured_int_peak": int_peak / 1e12,
+                         "note": "word ops (algorithmic, unduplicated) per second; peak = 152 SMs x 64 integer-ALU "
+                                 "lanes x max SM clock (measured_int_peak: sim_measure_int_peak, independent IADD3/LOP3 "
+                                 "chains on every SM); single-instance BSP is latency-bound, see "
+                                 "rows.phases for the cycle decomposition"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
             "rows": rows,
             "netlist": {k: info[k] for k in ("n_ops", "n_regs", "n_fibers", "n_processes", "fiber_cost_sum",

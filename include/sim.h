@@ -323,6 +323,13 @@ void sim_server_destroy(sim_server *s);
 
 const char *sim_last_error(void);
 
+/* Measured integer issue rate of the current device (the ALU roof of the
+ * interpreter): independent chains of three-input adds and three-input logic
+ * ops on every SM, `iters` iterations per thread, timed with CUDA events;
+ * *lane_ops_per_s = instructions x 32 lanes per second.  The paper has no
+ * counterpart.  Errors: BADARG, CUDA. */
+int sim_measure_int_peak(uint32_t iters, double *lane_ops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -16,7 +16,7 @@ import sys
 PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 LIB = os.path.join(PKG, "libgb300sim.so")
-SOURCES = ["kernels.cu", "runtime.cpp", "compiler.cpp", "noalloc.cu", "server.cpp", "codegen.cpp", "jit.cpp"]
+SOURCES = ["kernels.cu", "runtime.cpp", "compiler.cpp", "noalloc.cu", "server.cpp", "codegen.cpp", "jit.cpp", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

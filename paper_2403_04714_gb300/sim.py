@@ -94,6 +94,7 @@ EXPORTS = {
     "sim_last_error": (C.c_char_p, []),
     "sim_netlist_table": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "sim_state_digests_noalloc": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sim_measure_int_peak": (C.c_int, [C.c_uint32, C.c_void_p]),
     "sim_netlist_compile_generated": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]),
     "sim_phase_times": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
     "sim_server_config_default": (None, [C.c_void_p]),
@@ -174,6 +175,13 @@ def default_config(**kw) -> sim_config:
             v = ORDERS[v]
         setattr(cfg, k, v)
     return cfg
+
+
+def measure_int_peak(iters: int = 4096) -> float:
+    """sim_measure_int_peak: integer lane-operations per second of the current GPU."""
+    v = C.c_double()
+    _check(lib().sim_measure_int_peak(iters, C.byref(v)))
+    return v.value
 
 
 class Netlist:

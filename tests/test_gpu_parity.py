@@ -302,3 +302,10 @@ def test_batches_with_different_shared_memory_coexist(tiny_text, mid_text):
     ref = oracle.Sim(oracle.Net(text=mid_text), 1, 0)
     ref.run(3)
     assert big.state_digests()[0] == ref.digest()
+
+
+def test_measured_int_peak_is_plausible():
+    # the integer issue rate: at most one warp instruction per SM sub-partition
+    # and clock (152 SMs x 4 x 32 lanes x ~2.07 GHz = 40.3 T lane-ops/s)
+    v = sim.measure_int_peak(1 << 12)
+    assert 5e12 < v < 45e12, v
