@@ -492,6 +492,9 @@ __global__ void k_commit(DevProg P, DevState S, uint64_t t_end, const uint64_t* 
 // Advance the device-resident cycle base of a replayed graph chunk.
 __global__ void k_advance(uint64_t* t0_dev, uint64_t n) { *t0_dev += n; }
 
+// Set it (stream-ordered, so the host need not wait for a copy).
+__global__ void k_set_u64(uint64_t* p, uint64_t v) { *p = v; }
+
 // Reset instances [lo, lo+n) of buffer `par` to the initial state: register
 // init values, memory images, memory digest terms and held inputs.  Used by
 // the server when a job takes over instance slots of a pool.
@@ -683,6 +686,11 @@ cudaError_t launch_reset_slots(cudaStream_t st, const DevProg& P, const DevState
                                uint64_t mem_words, const uint64_t* mem_init_dig, uint64_t rom_init_dig) {
     k_reset_slots<<<256, 256, 0, st>>>(P, S, par, lo, n, reg_init, mem_image, mem_word_off, mem_words, mem_init_dig,
                                        rom_init_dig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_u64(cudaStream_t st, uint64_t* p, uint64_t v) {
+    k_set_u64<<<1, 1, 0, st>>>(p, v);
     return cudaGetLastError();
 }
 

@@ -29,6 +29,7 @@ cudaError_t occupancy_clusters(int grid, int threads, size_t smem, uint32_t C, i
 cudaError_t launch_cycles_cl(bool digest, int grid, int threads, size_t smem, uint32_t C, cudaStream_t st,
                              const DevProg& P, const DevState& S, const LaunchArgs& A);
 cudaError_t launch_advance(cudaStream_t st, uint64_t* t0_dev, uint64_t n);
+cudaError_t launch_set_u64(cudaStream_t st, uint64_t* p, uint64_t v);
 cudaError_t launch_state_digest(cudaStream_t st, const DevProg& P, const DevState& S, uint32_t par,
                                 const uint64_t* mem_word_off, uint64_t mem_words, uint64_t* out, uint32_t n_inst);
 }  // namespace rtl
@@ -879,9 +880,9 @@ int step_persistent_graph(sim_batch* b, uint64_t n) {
         CUDA_TRY(e);
         b->pgraph_n = n;
     }
-    CUDA_TRY(cudaMemcpyAsync(b->t0_dev.p, &b->cycle, 8, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(launch_set_u64(b->stream, b->t0_dev.as<uint64_t>(), b->cycle));
     CUDA_TRY(cudaGraphLaunch(b->pgraph, b->stream));
-    b->kernels_launched += 2;
+    b->kernels_launched += 3;
     return SIM_OK;
 }
 
@@ -937,8 +938,8 @@ int step_graph(sim_batch* b, uint64_t n) {
         b->graph_chunk = chunk;
     }
     uint64_t done = 0;
-    CUDA_TRY(cudaMemcpyAsync(b->t0_dev.p, &b->cycle, 8, cudaMemcpyHostToDevice, b->stream));
-    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    CUDA_TRY(launch_set_u64(b->stream, b->t0_dev.as<uint64_t>(), b->cycle));
+    b->kernels_launched++;
     while (n - done >= chunk) {
         CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
         b->kernels_launched += chunk + 2;
@@ -1446,7 +1447,7 @@ int pool_create(sim_netlist* nl, uint32_t capacity, sim_batch** out) {
     if (!nl || !out || capacity == 0) return set_err(SIM_ERR_BADARG, "bad argument");
     sim_config saved = nl->cfg;
     nl->cfg.mode = SIM_MODE_LANE_INST;
-    nl->cfg.kernel = SIM_KERNEL_PER_CYCLE;
+    nl->cfg.kernel = SIM_KERNEL_PER_CYCLE_GRAPH;
     nl->cfg.digest_capacity = 0;
     int rc = sim_create_instances(nl, capacity, 0, nullptr, out);
     nl->cfg = saved;
