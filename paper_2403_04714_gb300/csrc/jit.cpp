@@ -66,6 +66,14 @@ std::string max_registers() {
     return m ? m : "80";
 }
 
+// The kernel entry's launch bound must leave every process function its
+// register cap: the largest CTA, in groups of 4 warps (one per SM
+// sub-partition), whose threads x cap fit the 65,536-register file.
+int max_threads() {
+    const int cap = std::max(16, std::min(255, atoi(max_registers().c_str())));
+    return std::max(128, std::min(1024, 65536 / (cap * 128) * 128));
+}
+
 int compile_unit(const GenUnit& u, std::vector<char>& cubin, std::string& err) {
     nvrtcProgram prog;
     const char* hdr[2] = {kEmbeddedAbiHeader, kEmbeddedRtHeader};
@@ -78,12 +86,7 @@ int compile_unit(const GenUnit& u, std::vector<char>& cubin, std::string& err) {
     std::vector<const char*> opts = {arch.c_str(), "-rdc=true", "--std=c++17", "-default-device", "-w"};
     std::string maxr = "--maxrregcount=" + max_registers();
     opts.push_back(maxr.c_str());
-    // the kernel entry's launch bound must leave every process function its
-    // register cap: the largest power-of-two CTA with cap x threads <= 65536
-    const int cap = std::max(16, std::min(255, atoi(max_registers().c_str())));
-    int threads = 1024;
-    while (threads > 32 && threads * cap > 65536) threads /= 2;
-    std::string thr = "-DRTLSIM_GEN_MAX_THREADS=" + std::to_string(threads);
+    std::string thr = "-DRTLSIM_GEN_MAX_THREADS=" + std::to_string(max_threads());
     opts.push_back(thr.c_str());
     nvrtcResult r = nvrtcCompileProgram(prog, int(opts.size()), opts.data());
     if (r != NVRTC_SUCCESS) {
@@ -141,7 +144,7 @@ int jit_compile(const std::vector<GenUnit>& units, const std::string& cache_dir,
     auto t0 = std::chrono::steady_clock::now();
     uint64_t h = 0xcbf29ce484222325ULL;
     h = fnv1a(h, kArch);
-    h = fnv1a(h, "maxrreg=" + max_registers());
+    h = fnv1a(h, "maxrreg=" + max_registers() + " threads=" + std::to_string(max_threads()));
     h = fnv1a(h, kEmbeddedAbiHeader);
     h = fnv1a(h, kEmbeddedRtHeader);
     for (auto& u : units) h = fnv1a(fnv1a(h, u.name), u.source);
