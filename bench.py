@@ -125,7 +125,8 @@ def dist_setup(n_gpus):
 
 def barrier(dist):
     import torch
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
     if dist:
         dist.barrier()
 
@@ -134,9 +135,16 @@ def max_over_ranks(dist, x):
     if not dist:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_rate(dist, world, units_per_rank, seconds):
+    """Whole-job rate of N independent replicas (weak scaling, no data-path
+    collective): the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(dist, seconds)
 
 
 def time_steps(batch, stream, steps, warmup, cycles, flush):
@@ -373,8 +381,7 @@ def main():
     barrier(dist)
     with ClockSampler(local) as clk:
         ms, launches = time_steps(b, stream, args.steps, args.warmup, args.cycles, flush)
-    total_s = max_over_ranks(dist, sum(ms) / 1000.0)
-    value = world * args.steps * args.cycles / total_s
+    value = replica_rate(dist, world, args.steps * args.cycles, sum(ms) / 1000.0)
     per_launch_s = sum(ms) / 1000.0 / max(1, launches)
     cycles_per_launch = args.steps * args.cycles / max(1, launches)
     ops = info["n_ops"]
@@ -393,8 +400,7 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.steps):
         b2.step_host(args.cycles, held_pinned, out_pinned)
-    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
-    e2e = {"value": world * args.steps * args.cycles / e2e_s, "unit": UNIT,
+    e2e = {"value": replica_rate(dist, world, args.steps * args.cycles, time.perf_counter() - t0), "unit": UNIT,
            "h2d_bytes_per_step": int(held.nbytes), "d2h_bytes_per_step": 8,
            "call": "sim_step_host (all inputs held from pinned host memory, state digest read back)"}
     del b2
