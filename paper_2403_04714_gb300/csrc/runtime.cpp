@@ -72,6 +72,18 @@ int sm_count() {
     return n;
 }
 
+// Dynamic shared memory a CTA of our kernels may use: the device's opt-in
+// limit less 1 KB for the kernels' static shared variables.
+size_t smem_limit() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 220 * 1024;
+    }
+    return size_t(v) - 1024;
+}
+
 // Shared memory a cluster CTA requests at least: more than half an SM's,
 // so that no SM holds two CTAs of the grid (a doubly loaded SM would be the
 // straggler of every cycle).
@@ -499,7 +511,7 @@ uint32_t resident_words(const Lowered& L, uint32_t total_warps) {
 int plan_launch_cluster(sim_batch* b) {
     const Lowered& L = b->nl->low;
     const ClusterPlan& cp = b->nl->cplan;
-    const size_t smem_cap = 220 * 1024;
+    const size_t smem_cap = smem_limit();
     b->warps = int(cp.W);
     b->threads = int(cp.W) * 32;
     b->grid = int(cp.grid);
@@ -530,7 +542,7 @@ int plan_launch_cluster(sim_batch* b) {
 int plan_launch(sim_batch* b) {
     const Lowered& L = b->nl->low;
     const int sms = sm_count();
-    const size_t smem_cap = 220 * 1024;
+    const size_t smem_cap = smem_limit();
     const uint32_t n_proc = uint32_t(b->nl->part.procs.size());
     if (b->mode == SIM_MODE_LANE_INST) {
         b->slot_words = L.max_b_slots * 32;

@@ -126,3 +126,21 @@ def test_cluster_barrier_timeout_is_reported(tiny_text):
     b2.sync()
     want, ref = oracle_digests(tiny_text, 1, 0, 100)
     assert np.array_equal(b2.regs(0), ref.regs())
+
+
+def test_cluster_save_restore(tiny_text):
+    # checkpoint taken from a cluster run resumes to the same trace
+    nl = sim.Netlist(tiny_text, mode="lane_op", cluster_size=4, warps_per_cta=2, target_processes=8,
+                     digest_capacity=301)
+    b = sim.Batch(nl, 1, seed=5)
+    b.step(100)
+    blob = b.save()
+    b.step(200)
+    b.sync()
+    first = b.digests(0, 101, 200)
+    b.restore(blob)
+    b.step(200)
+    b.sync()
+    assert np.array_equal(b.digests(0, 101, 200), first)
+    want, _ = oracle_digests(tiny_text, 5, 0, 300)
+    assert first_mismatch(first, want[101:301]) is None
