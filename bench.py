@@ -268,7 +268,7 @@ def served_row(n_jobs=40):
     for hs in handles.values():          # compile (or load from the cache) before the trace starts
         for h in hs:
             h.compile_generated("lane_inst")
-    trace = netgen.served_trace(n_jobs=n_jobs)
+    trace = netgen.served_trace(n_jobs=n_jobs, cycles_lo=1e3, cycles_hi=3e4)
     srv = sim.Server(pool_slots=1024, chunk_cycles=250)
     t0 = time.perf_counter()
     ids = []
@@ -291,8 +291,8 @@ def served_row(n_jobs=40):
     return {"value": work / makespan, "unit": "instance-cycles/s", "p50_s": pct(0.5), "p99_s": pct(0.99),
             "makespan_s": makespan, "jobs": n_jobs, "kernels": stats["kernels"],
             "trace": "Poisson 200 jobs/s, shapes tiny/mid/2x2-mesh weights 0.6/0.3/0.1 (pools of 4/2/1 "
-                     "netlists), instances log-uniform 1-1024, cycles log-uniform 100-3000 (scaled down "
-                     "from 1e3-1e6 to fit the bench), cap 150 GiB, 1024 slots per pool, 250-cycle steps"}
+                     "netlists), instances log-uniform 1-1024, cycles log-uniform 1e3-3e4 (upper end scaled down "
+                     "from 1e6 to fit the bench), cap 150 GiB, 1024 slots per pool, 250-cycle steps"}
 
 
 def run_cpu_baseline(path, cycles, seed=42):
