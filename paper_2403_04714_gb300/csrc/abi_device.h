@@ -67,6 +67,8 @@ struct DevProg {
     const uint32_t* warp_proc;  // process of each warp of the grid, kNoProc if idle
     const uint32_t* mir_off;    // per CTA: first mirror entry (grid+1 offsets)
     const uint32_t* mir_reg;    // register held by each mirror entry
+    const uint32_t* warp_off;   // per warp: start of its slots in its CTA's shared memory (64-bit words)
+    const uint32_t* warp_slots; // per warp: its slot words, the last one spare (program follows)
     uint32_t n_proc, n_in, n_reg, n_mem, n_wport;
 };
 
@@ -118,6 +120,7 @@ struct LaunchArgs {
     uint32_t cluster;           // CTAs per thread-block cluster (0 = no cluster exchange)
     uint32_t mirror_words;      // per-CTA mirror entries per buffer (64-bit words)
     uint32_t one_cluster;       // the grid is one cluster: cluster barrier instead of the grid barrier
+    uint32_t mirror_off;        // start of the mirror in a cluster CTA's shared memory (64-bit words)
 };
 
 }  // namespace rtl

@@ -434,10 +434,11 @@ __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, Launc
     __shared__ __align__(8) uint64_t cbar[2];
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t warp = blockIdx.x * A.warps_per_cta + wib;
-    const uint64_t region = (uint64_t)A.slot_words + A.prog_words / 2;
-    uint64_t* sl = smem + (uint64_t)wib * region;
-    uint32_t* prog = reinterpret_cast<uint32_t*>(sl + A.slot_words);
-    uint64_t* mirror = smem + (uint64_t)A.warps_per_cta * region;
+    // warps' areas packed by their own process's needs (slots, then program)
+    const uint32_t slot_words = P.warp_slots[warp];
+    uint64_t* sl = smem + P.warp_off[warp];
+    uint32_t* prog = reinterpret_cast<uint32_t*>(sl + slot_words);
+    uint64_t* mirror = smem + A.mirror_off;
     const uint32_t p = P.warp_proc[warp];
     if (p != kNoProc) {
         const uint4* src = reinterpret_cast<const uint4*>(P.c_words + P.c_off[p]);
@@ -469,7 +470,7 @@ __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, Launc
         if (rec && threadIdx.x == 0) rec[0] = globaltimer_ns();
         if (p != kNoProc) {
             const uint32_t par = uint32_t(t & 1);
-            task_lane_op_res<DIGEST>(P, S, p, 0, t, pending, sl, prog, lane, A.slot_words - 1,
+            task_lane_op_res<DIGEST>(P, S, p, 0, t, pending, sl, prog, lane, slot_words - 1,
                                      mirror + (uint64_t)par * A.mirror_words,
                                      smem_addr(mirror + (uint64_t)(par ^ 1) * A.mirror_words));
         }

@@ -168,8 +168,9 @@ struct sim_batch {
     uint64_t seed = 0, cycle = 0;
     // program tables
     DBuf s_ins, s_off, s_len, c_words, c_off, c_size, b_ins, b_off, b_len, mport_off, mport_id, mem_lg, mem_w, mem_base,
-        in_w, reg_cls, reg_idx, mem_word_off, warp_proc, mir_off, mir_reg;
+        in_w, reg_cls, reg_idx, mem_word_off, warp_proc, mir_off, mir_reg, warp_off, warp_slots;
     bool cluster = false;                   // cluster exchange kernel (k_cycles_cl)
+    uint32_t mirror_off = 0;                // cluster CTA layout: mirror start (64-bit words)
     // state
     DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, rom_dig, bar, err, t0_dev,
         scratch, P_dev, S_dev, phase;
@@ -518,11 +519,26 @@ int plan_launch_cluster(sim_batch* b) {
     b->max_grid = b->grid;
     b->n_tasks = uint32_t(b->nl->part.procs.size());
     b->slot_words = (L.max_s_slots + 2) & ~1u;
-    uint32_t pw = 0;
-    for (uint32_t p : cp.warp_proc)
-        if (p != kNoProc) pw = std::max(pw, L.c_size[p]);
-    b->prog_words = (pw + 3) & ~3u;
-    b->smem = size_t(cp.W) * (size_t(b->slot_words) * 8 + size_t(b->prog_words) * 4) + size_t(cp.mirror_words) * 16;
+    b->prog_words = 0;
+    // pack each CTA's warps by their own process's slots (plus one spare) and
+    // program; every area starts on 16 bytes (even slot words, programs in
+    // multiples of 4 words)
+    std::vector<uint32_t> warp_off(cp.warp_proc.size(), 0), warp_slots(cp.warp_proc.size(), 0);
+    uint64_t max_cta = 0;
+    for (uint32_t c = 0; c < cp.grid; c++) {
+        uint64_t off = 0;
+        for (uint32_t w = 0; w < cp.W; w++) {
+            const size_t i = size_t(c) * cp.W + w;
+            const uint32_t p = cp.warp_proc[i];
+            warp_off[i] = uint32_t(off);
+            if (p == kNoProc) continue;
+            warp_slots[i] = (L.s_slots[p] + 2) & ~1u;
+            off += warp_slots[i] + L.c_size[p] / 2;
+        }
+        max_cta = std::max(max_cta, off);
+    }
+    b->mirror_off = uint32_t(max_cta);
+    b->smem = size_t(max_cta) * 8 + size_t(cp.mirror_words) * 16;
     b->smem = std::max(b->smem, kClusterCtaSmemMin);
     if (b->smem > smem_cap)
         return set_err(SIM_ERR_CAPACITY, "cluster CTA needs " + std::to_string(b->smem) +
@@ -533,6 +549,11 @@ int plan_launch_cluster(sim_batch* b) {
     if (uint64_t(n_clusters) * cp.C < uint64_t(b->grid))
         return set_err(SIM_ERR_CAPACITY, std::to_string(cp.grid / cp.C) + " clusters of " + std::to_string(cp.C) +
                                              " CTAs requested, " + std::to_string(n_clusters) + " can be resident");
+    int rc;
+    if ((rc = upload(b->warp_off, warp_off, b->stream)) || (rc = upload(b->warp_slots, warp_slots, b->stream))) return rc;
+    b->P.warp_off = b->warp_off.as<uint32_t>();
+    b->P.warp_slots = b->warp_slots.as<uint32_t>();
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
     b->cluster = true;
     return SIM_OK;
 }
@@ -810,6 +831,7 @@ LaunchArgs base_args(sim_batch* b) {
         A.cluster = b->nl->cplan.C;
         A.mirror_words = b->nl->cplan.mirror_words;
         A.one_cluster = uint32_t(b->grid) == b->nl->cplan.C;
+        A.mirror_off = b->mirror_off;
     }
     return A;
 }
