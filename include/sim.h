@@ -110,7 +110,10 @@ typedef struct sim_config {
     uint32_t cluster_size;      /* 0 = off; 2..16: thread-block clusters of this many CTAs exchange register values
                                  * through distributed shared memory (LANE_OP, bytecode, persistent kernel, one
                                  * instance; see sim_create_instances).  A grid of one cluster synchronises with
-                                 * the cluster's barrier instead of the grid barrier. */
+                                 * the cluster's barrier instead of the grid barrier.  Cluster grids are plain
+                                 * (not cooperative) launches: a step that runs while another persistent
+                                 * launch holds SMs may not get all its CTAs at once and then ends with
+                                 * SIM_ERR_TIMEOUT (never a hang). */
     uint32_t reserved[3];
 } sim_config;
 
