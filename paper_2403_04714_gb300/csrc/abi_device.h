@@ -121,6 +121,8 @@ struct LaunchArgs {
     uint32_t mirror_words;      // per-CTA mirror entries per buffer (64-bit words)
     uint32_t one_cluster;       // the grid is one cluster: cluster barrier instead of the grid barrier
     uint32_t mirror_off;        // start of the mirror in a cluster CTA's shared memory (64-bit words)
+    uint32_t grid;              // launch shape the batch planned (checked by the cluster kernel on entry)
+    uint32_t smem_bytes;        // dynamic shared memory the batch planned
 };
 
 }  // namespace rtl

@@ -158,6 +158,18 @@ __device__ __forceinline__ void st_peer_u64(uint32_t local_addr, uint32_t rank, 
     asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(ra), "l"(v) : "memory");
 }
 
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+    uint32_t n;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return n;
+}
+
+__device__ __forceinline__ uint32_t dynamic_smem_bytes() {
+    uint32_t n;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(n));
+    return n;
+}
+
 // Hardware cluster barrier (all threads of every CTA of the cluster); used
 // only where every thread is known to arrive: kernel entry and exit.
 __device__ __forceinline__ void cluster_sync_all() {
@@ -432,6 +444,15 @@ template <bool DIGEST>
 __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
     __shared__ __align__(8) uint64_t cbar[2];
+    // the lowering addresses peers by rank within clusters of A.cluster CTAs
+    // and the warps' areas by the planned layout: a launch of any other shape
+    // (grid, block, cluster or shared memory; the same for every CTA) does
+    // nothing but report it
+    if (cluster_nctarank() != A.cluster || gridDim.x != A.grid || gridDim.x % A.cluster != 0 ||
+        blockDim.x != A.warps_per_cta * 32 || dynamic_smem_bytes() < A.smem_bytes) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) atomicCAS(S.err, 0, (int32_t)SIM_ERR_STATE);
+        return;
+    }
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const uint32_t warp = blockIdx.x * A.warps_per_cta + wib;
     // warps' areas packed by their own process's needs (slots, then program)
@@ -630,7 +651,7 @@ cudaError_t prepare_cluster_kernel(size_t smem, uint32_t C) {
 }
 
 static cudaLaunchConfig_t cluster_config(int grid, int threads, size_t smem, uint32_t C, cudaStream_t st,
-                                         cudaLaunchAttribute* at, bool cooperative) {
+                                         cudaLaunchAttribute* at) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -640,40 +661,33 @@ static cudaLaunchConfig_t cluster_config(int grid, int threads, size_t smem, uin
     at[0].val.clusterDim.x = C;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
-    at[1].id = cudaLaunchAttributeCooperative;
-    at[1].val.cooperative = 1;
     cfg.attrs = at;
-    cfg.numAttrs = cooperative ? 2 : 1;
+    cfg.numAttrs = 1;
     return cfg;
 }
 
 // Clusters of C CTAs that can be resident at once.
 cudaError_t occupancy_clusters(int grid, int threads, size_t smem, uint32_t C, int* n_clusters) {
-    cudaLaunchAttribute at[2];
-    cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, nullptr, at, false);
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, nullptr, at);
     return cudaOccupancyMaxActiveClusters(n_clusters, cycles_cl_fn(false), &cfg);
 }
 
 // A grid of several clusters synchronises with the grid barrier, so all of
-// them must be resident: cooperative launch when the driver accepts it with
-// clusters, else a plain cluster launch (the planner checked residency and
-// the barrier's wait is bounded either way).
+// them must be resident at once: the planner checked that with the cluster
+// occupancy query (one CTA per SM), and the barrier's wait is bounded, so a
+// grid that is not resident ends with SIM_ERR_TIMEOUT rather than a hang.
+// Plain cluster launch: the cooperative attribute together with a cluster
+// dimension made the launch fail under the profiler with a device fault.
 cudaError_t launch_cycles_cl(bool digest, int grid, int threads, size_t smem, uint32_t C, cudaStream_t st,
                              const DevProg& P, const DevState& S, const LaunchArgs& A) {
     DevProg p = P;
     DevState s = S;
     LaunchArgs a = A;
     void* args[] = {&p, &s, &a};
-    cudaLaunchAttribute at[2];
-    const bool coop = grid > int(C);
-    cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, st, at, coop);
-    cudaError_t e = cudaLaunchKernelExC(&cfg, cycles_cl_fn(digest), args);
-    if (e != cudaSuccess && coop) {
-        cudaGetLastError();
-        cfg = cluster_config(grid, threads, smem, C, st, at, false);
-        e = cudaLaunchKernelExC(&cfg, cycles_cl_fn(digest), args);
-    }
-    return e;
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, st, at);
+    return cudaLaunchKernelExC(&cfg, cycles_cl_fn(digest), args);
 }
 
 cudaError_t launch_commit(int grid, cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t_end,

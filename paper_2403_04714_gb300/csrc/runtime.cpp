@@ -832,6 +832,8 @@ LaunchArgs base_args(sim_batch* b) {
         A.mirror_words = b->nl->cplan.mirror_words;
         A.one_cluster = uint32_t(b->grid) == b->nl->cplan.C;
         A.mirror_off = b->mirror_off;
+        A.grid = uint32_t(b->grid);
+        A.smem_bytes = uint32_t(b->smem);
     }
     return A;
 }
