@@ -166,8 +166,10 @@ int sim_netlist_compile_generated(sim_netlist *nl, int32_t mode, double *seconds
  *  11 register index within its class (u32)
  *  12 LANE_OP slot count of each process (u32)    13 LANE_INST slot count (u32)
  *  14 LANE_OP compact programs kept in shared memory (u32 words: per process
- *     a step table, first instruction | count << 16, padded to 4 words, then
- *     the 16-byte instructions)                    15 first word of each (u32)
+ *     the step count n, n step words (first instruction | count << 16 |
+ *     flags: bit 31 not operators only, bit 30 leaves only, up to 128 of
+ *     them), padded to a multiple of 4 words, then the 16-byte instructions)
+ *                                                  15 first word of each (u32)
  *  16 words of each (u32)
  *  Cluster exchange (cluster_size > 0; empty otherwise):
  *  17 process of each warp of the grid (u32, 0xffffffff = idle)

@@ -39,10 +39,14 @@ struct DIns {
 };
 
 // LANE_OP step word of a shared-memory program: first instruction (bits
-// 0-15), instruction count (bits 16-21), and this flag when the step holds
-// anything other than the 13 operators (leaves, memory reads, stores).
+// 0-15), instruction count (bits 16-23), kStepGeneric when the step holds
+// anything other than the 13 operators (leaves, memory reads, stores), and
+// kStepLeaf when it holds only leaves (register, mirror, input, constant):
+// such a step may hold up to kLeafStepMax instructions, four per lane.
 constexpr uint32_t kStepGeneric = 1u << 31;
-constexpr uint32_t kStepCountMask = 0x3fu;
+constexpr uint32_t kStepLeaf = 1u << 30;
+constexpr uint32_t kStepCountMask = 0xffu;
+constexpr uint32_t kLeafStepMax = 128;
 
 // Program tables of one lowered netlist (device pointers).
 struct DevProg {

@@ -723,7 +723,7 @@ struct Item {
     int32_t id;        // node id / register / port / memory
     int level;
     uint8_t op;        // for sorting within a level
-    int phase = 0;     // LANE_OP order: 0 leaves and commits, 1 operators, 2 stores and write records
+    int phase = 0;     // LANE_OP order: 0 memory commits, 1 leaves, 2 operators, 3 stores and write records
 };
 
 constexpr uint16_t kNoSlot = 0xffff;
@@ -746,6 +746,41 @@ struct SlotAlloc {
     }
     void put(uint16_t s) { free_list.push_back(s); }
 };
+
+}  // namespace
+
+namespace {
+
+// One step of a shared-memory program.
+struct CStep {
+    uint32_t flags = 0;
+    std::vector<DIns> ins;
+};
+
+// Program layout: word 0 = step count n, words 1..n = step words (first
+// instruction | count << 16 | flags), padded to a multiple of 4 words, then
+// the 16-byte instructions.
+int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words, std::string& err) {
+    const uint32_t nb = uint32_t(steps.size()), tw = (nb + 4) & ~3u;
+    const size_t base = words.size();
+    words.resize(base + tw, 0);
+    words[base] = nb;
+    uint32_t first = 0;
+    for (uint32_t b = 0; b < nb; b++) {
+        words[base + 1 + b] = first | (uint32_t(steps[b].ins.size()) << 16) | steps[b].flags;
+        for (const DIns& d : steps[b].ins) {
+            uint32_t w4[4];
+            memcpy(w4, &d, 16);
+            words.insert(words.end(), w4, w4 + 4);
+        }
+        first += uint32_t(steps[b].ins.size());
+    }
+    if (first > 0xffff) {
+        err = "process has too many instructions for one program";
+        return SIM_ERR_CAPACITY;
+    }
+    return SIM_OK;
+}
 
 }  // namespace
 
@@ -789,16 +824,17 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
                 }
             }
         }
-        // steps: leaves and memory commits first, then the operators by level,
+        // steps: memory commits, then leaves, then the operators by level,
         // then register stores and write records (their values stay in slots
         // until the end); within a level by operator kind (less divergence in a
         // step), then id.  Operator steps hold operators only, apart from the
-        // rare memory reads, so the interpreter runs them without branches.
+        // rare memory reads, so the interpreter runs them without branches;
+        // leaf steps hold leaves only, so their loads can all be in flight.
         auto phase = [&](const Item& it) {
-            if (it.kind == 1 || it.kind == 2) return 2;
+            if (it.kind == 1 || it.kind == 2) return 3;
             if (it.kind == 3) return 0;
             const uint8_t op = nl.nodes[it.id].op;
-            return (op == OP_INPUT || op == OP_REG || op == OP_CONST) ? 0 : 1;
+            return (op == OP_INPUT || op == OP_REG || op == OP_CONST) ? 1 : 2;
         };
         for (auto& it : items) it.phase = phase(it);
         std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) {
@@ -817,7 +853,7 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             for (size_t i = 0; i < items.size(); i++) {
                 // operators never share a step with their own operands; the
                 // leaves and the stores have no dependences among themselves
-                const int lv = items[i].phase == 1 ? items[i].level : 0;
+                const int lv = items[i].phase == 2 ? items[i].level : 0;
                 if (lv != cur_level || items[i].phase != cur_phase || fill == 32) {
                     nb++;
                     fill = 0;
@@ -935,28 +971,31 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             }
             out.s_len[p] = nb;
             out.s_slots[p] = std::max<uint32_t>(1, A.next);
-            // compact copy: bundle table, then the occupied lanes of each row
+            // compact copy: the occupied lanes of each row; up to four rows of
+            // leaves (which never share a slot: all their consumers come later)
+            // form one wide step of up to 128 instructions
             std::vector<uint32_t> count(nb, 0);
             for (size_t k = 0; k < items.size(); k++) count[bundle[k]]++;
-            const uint32_t table_words = (nb + 3) / 4 * 4;
-            out.c_off[p] = uint32_t(out.c_words.size());
-            std::vector<uint32_t> prog(table_words, 0);
-            uint32_t first = 0;
+            std::vector<CStep> steps;
             for (uint32_t b = 0; b < nb; b++) {
                 const DIns* row = &out.s_ins[(size_t(out.s_off[p]) + b) * 32];
-                bool operators_only = true;
-                for (uint32_t l = 0; l < count[b]; l++) operators_only &= row[l].op >= D_ADD && row[l].op <= D_CONCAT;
-                prog[b] = first | (count[b] << 16) | (operators_only ? 0u : kStepGeneric);
+                bool operators_only = true, leaves_only = count[b] > 0;
                 for (uint32_t l = 0; l < count[b]; l++) {
-                    uint32_t w[4];
-                    memcpy(w, &row[l], 16);
-                    prog.insert(prog.end(), w, w + 4);
+                    operators_only &= row[l].op >= D_ADD && row[l].op <= D_CONCAT;
+                    leaves_only &= row[l].op == D_LDR || row[l].op == D_LDI || row[l].op == D_CONST;
                 }
-                first += count[b];
+                const uint32_t flags = (operators_only ? 0u : kStepGeneric) | (leaves_only ? kStepLeaf : 0u);
+                if (leaves_only && !steps.empty() && (steps.back().flags & kStepLeaf) &&
+                    steps.back().ins.size() + count[b] <= kLeafStepMax) {
+                    steps.back().ins.insert(steps.back().ins.end(), row, row + count[b]);
+                    continue;
+                }
+                steps.push_back(CStep{flags, std::vector<DIns>(row, row + count[b])});
             }
-            if (first > 0xffff) { err = "process has too many instructions for one program"; return SIM_ERR_CAPACITY; }
-            out.c_size[p] = uint32_t(prog.size());
-            out.c_words.insert(out.c_words.end(), prog.begin(), prog.end());
+            out.c_off[p] = uint32_t(out.c_words.size());
+            int rc = append_program(steps, out.c_words, err);
+            if (rc) return rc;
+            out.c_size[p] = uint32_t(out.c_words.size()) - out.c_off[p];
             if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
         }
         // ---- LANE_INST: sequential list in depth-first post-order from each
@@ -1048,20 +1087,15 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
 // ---------------------------------------------------------------------------
 namespace {
 
-struct Step {
-    uint32_t flags = 0;
-    std::vector<DIns> ins;
-};
-
 // Steps of process p from its compact program.
-std::vector<Step> read_steps(const Lowered& low, size_t p) {
+std::vector<CStep> read_steps(const Lowered& low, size_t p) {
     const uint32_t* w = low.c_words.data() + low.c_off[p];
-    const uint32_t nb = low.s_len[p], tw = (nb + 3) & ~3u;
+    const uint32_t nb = w[0], tw = (nb + 4) & ~3u;
     const DIns* ins = reinterpret_cast<const DIns*>(w + tw);
-    std::vector<Step> steps(nb);
+    std::vector<CStep> steps(nb);
     for (uint32_t b = 0; b < nb; b++) {
-        const uint32_t e = w[b], first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        steps[b].flags = e & kStepGeneric;
+        const uint32_t e = w[1 + b], first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
+        steps[b].flags = e & (kStepGeneric | kStepLeaf);
         steps[b].ins.assign(ins + first, ins + first + cnt);
     }
     return steps;
@@ -1085,7 +1119,7 @@ int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_
     for (size_t p = 0; p < NP; p++)
         for (int32_t f : part.procs[p])
             if (part.fibers[f].reg >= 0) proc_of_reg[part.fibers[f].reg] = int32_t(p);
-    std::vector<std::vector<Step>> steps(NP);
+    std::vector<std::vector<CStep>> steps(NP);
     std::vector<std::vector<uint32_t>> reads(NP);
     for (size_t p = 0; p < NP; p++) {
         steps[p] = read_steps(low, p);
@@ -1290,41 +1324,33 @@ int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_
                 }
             }
         for (size_t k = 0; k < stx.size(); k += 32) {
-            Step st;
+            CStep st;
             st.flags = kStepGeneric;
             st.ins.assign(stx.begin() + k, stx.begin() + std::min(stx.size(), k + 32));
             steps[p].push_back(std::move(st));
         }
     }
 
-    // rebuild the bundle rows and the compact programs
+    // rebuild the bundle rows (32 instructions each: a wide leaf step takes
+    // several) and the compact programs
     low.s_ins.clear();
     low.c_words.clear();
     low.max_bundles = 0;
     for (size_t p = 0; p < NP; p++) {
-        const uint32_t nb = uint32_t(steps[p].size()), tw = (nb + 3) & ~3u;
         low.s_off[p] = uint32_t(low.s_ins.size() / 32);
-        low.s_len[p] = nb;
-        low.max_bundles = std::max(low.max_bundles, nb);
-        low.c_off[p] = uint32_t(low.c_words.size());
-        std::vector<uint32_t> prog(tw, 0);
-        uint32_t first = 0;
-        for (uint32_t b = 0; b < nb; b++) {
-            const auto& st = steps[p][b];
-            const size_t base = low.s_ins.size();
-            low.s_ins.resize(base + 32, DIns{});
-            std::copy(st.ins.begin(), st.ins.end(), low.s_ins.begin() + base);
-            prog[b] = first | (uint32_t(st.ins.size()) << 16) | st.flags;
-            for (const DIns& d : st.ins) {
-                uint32_t w4[4];
-                memcpy(w4, &d, 16);
-                prog.insert(prog.end(), w4, w4 + 4);
+        for (const auto& st : steps[p])
+            for (size_t k = 0; k < std::max<size_t>(1, st.ins.size()); k += 32) {
+                const size_t base = low.s_ins.size();
+                low.s_ins.resize(base + 32, DIns{});
+                const size_t n = std::min<size_t>(32, st.ins.size() - std::min(k, st.ins.size()));
+                std::copy(st.ins.begin() + k, st.ins.begin() + k + n, low.s_ins.begin() + base);
             }
-            first += uint32_t(st.ins.size());
-        }
-        if (first > 0xffff) { err = "process has too many instructions for one program"; return SIM_ERR_CAPACITY; }
-        low.c_size[p] = uint32_t(prog.size());
-        low.c_words.insert(low.c_words.end(), prog.begin(), prog.end());
+        low.s_len[p] = uint32_t(low.s_ins.size() / 32) - low.s_off[p];
+        low.max_bundles = std::max(low.max_bundles, low.s_len[p]);
+        low.c_off[p] = uint32_t(low.c_words.size());
+        int rc = append_program(steps[p], low.c_words, err);
+        if (rc) return rc;
+        low.c_size[p] = uint32_t(low.c_words.size()) - low.c_off[p];
     }
     return SIM_OK;
 }

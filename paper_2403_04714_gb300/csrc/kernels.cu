@@ -316,6 +316,15 @@ __device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, con
     }
 }
 
+// Value of a leaf instruction (register, mirror entry, input, constant).
+__device__ __forceinline__ uint64_t leaf_value(const Dec& d, const DevProg& P, const DevState& S, uint32_t inst,
+                                               uint64_t t, uint64_t key, const uint64_t* mir_cur) {
+    if (d.op == D_LDR) return load_reg(S, uint32_t(t & 1), d.c, d.b | (d.x << 16), inst);
+    if (d.op == D_LDM) return mir_cur[d.b | (d.x << 16)];
+    if (d.op == D_LDI) return stimulus(P, S, key, d.imm, inst, t, d.w);
+    return (uint64_t)d.imm | ((uint64_t)d.a << 32) | ((uint64_t)d.b << 48);   // D_CONST
+}
+
 template <bool DIGEST>
 __device__ __forceinline__ void finish_lane_op(const DevState& S, uint32_t p, uint32_t inst, uint64_t t, int32_t col,
                                                uint32_t lane, uint64_t dacc) {
@@ -345,9 +354,9 @@ __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, ui
     finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
 
-// Program resident in shared memory: `prog` holds the step table (first
-// instruction | count << 16 | kStepGeneric) followed by the instructions,
-// 16-byte aligned.  Operator-only steps run on all 32 lanes without a branch:
+// Program resident in shared memory: `prog` holds the step count, the step
+// table (first instruction | count << 16 | flags) and, 16-byte aligned, the
+// instructions.  Operator-only steps run on all 32 lanes without a branch:
 // lanes past the step's count repeat its first instruction and write the
 // spare slot `dummy` (the last word of the warp's slot region), which no
 // instruction reads.
@@ -359,20 +368,39 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     const uint64_t key = S.key[inst];
     const int32_t col = DIGEST ? S.track[inst] : -1;
     uint64_t dacc = 0;
-    const uint32_t nb = P.s_len[p];
-    const uint4* ins = reinterpret_cast<const uint4*>(prog + ((nb + 3) & ~3u));
-    uint32_t e = nb ? prog[0] : 0;
+    const uint32_t nb = prog[0];
+    const uint32_t* table = prog + 1;
+    const uint4* ins = reinterpret_cast<const uint4*>(prog + ((nb + 4) & ~3u));
+    uint32_t e = nb ? table[0] : 0;
     for (uint32_t b = 0; b < nb; b++) {
-        const uint32_t e_next = b + 1 < nb ? prog[b + 1] : 0;
+        const uint32_t e_next = b + 1 < nb ? table[b + 1] : 0;
         const uint32_t first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        if (e & kStepGeneric) {
-            if (lane < cnt)
-                exec_lane_op<DIGEST>(decode(ins[first + lane]), P, S, inst, t, key, col, pending, sl, dacc, mir_cur,
-                                     mir_nxt);
-        } else {
+        if (!(e & kStepGeneric)) {
+            // operator step: all 32 lanes, no branch (idle lanes write the spare slot)
             const bool on = lane < cnt;
             const Dec d = decode(ins[on ? first + lane : first]);
             sl[on ? d.dst : dummy] = alu_select(d.op, sl[d.a], sl[d.b], sl[d.c], d.x) & wmask(d.w);
+        } else if (e & kStepLeaf) {
+            // up to four leaves per lane, every load in flight before the
+            // first value is stored; idle lanes write the spare slot
+            uint64_t v[4];
+            uint32_t dst[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) {
+                const uint32_t i = k * 32 + lane;
+                v[k] = 0;
+                dst[k] = dummy;
+                if (i < cnt) {
+                    const Dec d = decode(ins[first + i]);
+                    dst[k] = d.dst;
+                    v[k] = leaf_value(d, P, S, inst, t, key, mir_cur);
+                }
+            }
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) sl[dst[k]] = v[k];
+        } else if (lane < cnt) {
+            exec_lane_op<DIGEST>(decode(ins[first + lane]), P, S, inst, t, key, col, pending, sl, dacc, mir_cur,
+                                 mir_nxt);
         }
         __syncwarp();
         e = e_next;

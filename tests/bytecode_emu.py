@@ -37,24 +37,33 @@ class Emu:
             # rebuild 32-wide rows from the shared-memory program format
             words = netlist.table("c_words")
             c_off, c_size = netlist.table("c_off"), netlist.table("c_size")
-            nb_all = netlist.table("s_len")
             rows = []
             self.off = []
             import numpy as np
             from paper_2403_04714_gb300.sim import DINS
+            lens = []
             for p in range(len(c_off)):
+                # word 0: step count; then the step words; instructions from
+                # the next multiple of 4 words.  A wide leaf step (up to 128
+                # independent leaves) becomes several 32-lane rows.
                 prog = words[int(c_off[p]):int(c_off[p]) + int(c_size[p])]
-                nb = int(nb_all[p])
-                table = prog[:nb]
-                ins = prog[(nb + 3) // 4 * 4:].copy().view(DINS)
+                nb = int(prog[0])
+                table = prog[1:1 + nb]
+                ins = prog[(nb + 4) // 4 * 4:].copy().view(DINS)
                 self.off.append(len(rows) // 32)
+                n_rows = 0
                 for e in table:
-                    first, cnt = int(e) & 0xffff, (int(e) >> 16) & 0x3f
-                    row = np.zeros(32, dtype=DINS)
-                    row[:cnt] = ins[first:first + cnt]
-                    rows.extend(row)
+                    first, cnt = int(e) & 0xffff, (int(e) >> 16) & 0xff
+                    assert cnt <= 32 or (int(e) >> 30) & 1, "only leaf steps may exceed 32 lanes"
+                    for k in range(0, max(cnt, 1), 32):
+                        row = np.zeros(32, dtype=DINS)
+                        n = min(32, cnt - k)
+                        row[:n] = ins[first + k:first + k + n]
+                        rows.extend(row)
+                        n_rows += 1
+                lens.append(n_rows)
             self.ins = np.array(rows, dtype=DINS)
-            self.len = nb_all
+            self.len = lens
             self.nslots = netlist.table("s_slots")
             mode = "lane_op"
         elif mode == "lane_op":
