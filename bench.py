@@ -429,7 +429,15 @@ def main():
             del bk, nlk
         # batched: same netlist x 4096 instances, lane = instance, both lowerings
         for low in (("generated", "bytecode") if "batched" in want else ()):
-            nlb = sim.Netlist(text, mode="lane_inst", lowering=low, kernel="persistent_graph")
+            cfg_b = {"mode": "lane_inst", "lowering": low}
+            tuned_b = None
+            if low == "generated":
+                # instances per CTA (32 x warps) and the task order, by measurement
+                cands = [dict(cfg_b, warps_per_cta=w, task_order=o)
+                         for w, o in ((8, "process_major"), (12, "process_major"), (8, "group_major"))]
+                tuned_b = autotune.autotune(text, 4096, candidates=cands, cycles=40)
+                cfg_b = tuned_b["config"]
+            nlb = sim.Netlist(text, kernel="persistent_graph", **cfg_b)
             comp = nlb.compile_generated("lane_inst") if low == "generated" else None
             bb = sim.Batch(nlb, 4096, seed=42, stream=stream)
             cyc = args.batched_cycles if low == "generated" else max(10, args.batched_cycles // 5)
@@ -443,6 +451,8 @@ def main():
                 "alu_frac": ib["n_ops"] * ic / peak,
                 "hbm_gbs_algorithmic": ic * 2 * STATE_BYTES_MID / 1e9,
                 "compile": comp,
+                "autotuned": None if tuned_b is None else {"config": tuned_b["config"], "cached": tuned_b["cached"],
+                                                           "candidates": tuned_b["results"]},
             }
             del bb, nlb
         if "single" in want:
