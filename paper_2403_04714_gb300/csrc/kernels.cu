@@ -524,7 +524,15 @@ __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, Launc
                                      smem_addr(mirror + (uint64_t)(par ^ 1) * A.mirror_words));
         }
         const bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
-        if (A.one_cluster)
+        if (A.one_cluster && A.skip_cta < 0) {
+            // every thread of the cluster reaches this point every cycle (no
+            // early exit exists on this path), so the hardware cluster
+            // barrier cannot wait forever; release/acquire at cluster scope
+            // orders the cycle's shared, distributed and global stores
+            if (rec && threadIdx.x == 0) rec[1] = globaltimer_ns();
+            cluster_sync_all();
+            if (rec && threadIdx.x == 0) rec[2] = globaltimer_ns();
+        } else if (A.one_cluster)
             ok = cluster_barrier(cbar, c, A.cluster, A.timeout_ns, S.err, skip, rec ? rec + 1 : nullptr);
         else
             ok = grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip, rec ? rec + 1 : nullptr);
