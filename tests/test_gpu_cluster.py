@@ -144,3 +144,21 @@ def test_cluster_save_restore(tiny_text):
     assert np.array_equal(b.digests(0, 101, 200), first)
     want, _ = oracle_digests(tiny_text, 5, 0, 300)
     assert first_mismatch(first, want[101:301]) is None
+
+
+def test_cluster_grid_barrier_timeout_is_reported(tiny_text):
+    # a grid of two clusters: the cluster holding the skipping CTA withholds
+    # its arrival at the grid counter; every cluster's bounded wait expires
+    nl = sim.Netlist(tiny_text, mode="lane_op", cluster_size=2, warps_per_cta=2, target_processes=8)
+    assert nl.table("cluster_plan")[2] == 4
+    b = sim.Batch(nl, 1, seed=1)
+    b.debug_skip_arrival(20)
+    b.step(10)
+    with pytest.raises(sim.SimError) as e:
+        b.sync()
+    assert e.value.name == "SIM_ERR_TIMEOUT"
+    b2 = sim.Batch(nl, 1, seed=1)
+    b2.step(100)
+    b2.sync()
+    want, ref = oracle_digests(tiny_text, 1, 0, 100)
+    assert np.array_equal(b2.regs(0), ref.regs())
