@@ -18,8 +18,11 @@ int pool_create(sim_netlist* nl, uint32_t capacity, sim_batch** out);
 // Give slots [lo, lo+n) to a job: stimulus keys of instances 0..n-1 of `seed`,
 // cycle origin = the pool's current cycle, state reset to the initial state.
 int pool_admit(sim_batch* b, uint32_t lo, uint32_t n, uint64_t seed);
-// Enqueue `n` cycles for every slot (asynchronous on the pool's stream).
+// Enqueue `n` cycles for the active slots (asynchronous on the pool's stream).
 int pool_step(sim_batch* b, uint64_t n);
+// Simulate only instance groups [0, n_groups) (32 slots each) from the next
+// step on: slots are taken first-fit, so the occupied ones sit at the front.
+int pool_set_active(sim_batch* b, uint32_t n_groups);
 // State digests of slots [lo, lo+n) (synchronises the pool's stream).
 int pool_digests(sim_batch* b, uint32_t lo, uint32_t n, uint64_t* out);
 // Device bytes a pool of `capacity` slots of this netlist holds.

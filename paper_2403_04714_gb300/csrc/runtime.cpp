@@ -194,6 +194,7 @@ struct sim_batch {
     // graph replay of per-cycle launches
     cudaGraphExec_t graph = nullptr;
     uint32_t graph_chunk = 0;
+    uint32_t graph_tasks = 0;              // tasks per cycle the graph was captured for
     cudaGraphExec_t pgraph = nullptr;      // captured persistent step
     uint64_t pgraph_n = 0;
     DevState pgraph_state{};
@@ -946,7 +947,8 @@ int step_graph(sim_batch* b, uint64_t n) {
     const uint32_t chunk = 64;
     int src = sync_state_view(b);
     if (src) return src;
-    if (!b->graph || b->graph_chunk != chunk || memcmp(&b->graph_state, &b->S, sizeof(DevState)) != 0) {
+    if (!b->graph || b->graph_chunk != chunk || b->graph_tasks != b->n_tasks ||
+        memcmp(&b->graph_state, &b->S, sizeof(DevState)) != 0) {
         b->graph_state = b->S;
         if (b->graph) cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -972,6 +974,7 @@ int step_graph(sim_batch* b, uint64_t n) {
         cudaGraphDestroy(g);
         CUDA_TRY(e);
         b->graph_chunk = chunk;
+        b->graph_tasks = b->n_tasks;
     }
     uint64_t done = 0;
     CUDA_TRY(launch_set_u64(b->stream, b->t0_dev.as<uint64_t>(), b->cycle));
@@ -1530,6 +1533,13 @@ int pool_admit(sim_batch* b, uint32_t lo, uint32_t n, uint64_t seed) {
 }
 
 int pool_step(sim_batch* b, uint64_t n) { return sim_step(b, n); }
+
+int pool_set_active(sim_batch* b, uint32_t n_groups) {
+    if (!b || !b->pool || b->mode != SIM_MODE_LANE_INST || n_groups == 0 || uint64_t(n_groups) * 32 > b->I)
+        return set_err(SIM_ERR_BADARG, "bad active group count");
+    b->n_tasks = uint32_t(b->nl->part.procs.size()) * n_groups;
+    return SIM_OK;
+}
 
 void pool_extra_free(PoolExtra* x) { delete x; }
 

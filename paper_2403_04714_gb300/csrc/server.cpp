@@ -227,11 +227,16 @@ void sim_server::run() {
             Pool& p = *pp;
             if (!p.inflight && !p.active.empty()) {
                 uint64_t n = cfg.chunk_cycles;
+                uint32_t hi = 0;       // slots in use end here (first-fit keeps them at the front)
                 {
                     std::lock_guard<std::mutex> g(mu);
-                    for (uint64_t id : p.active) n = std::min(n, jobs[id]->spec.n_cycles - jobs[id]->cycles_done);
+                    for (uint64_t id : p.active) {
+                        n = std::min(n, jobs[id]->spec.n_cycles - jobs[id]->cycles_done);
+                        hi = std::max(hi, jobs[id]->slot_lo + jobs[id]->spec.n_inst);
+                    }
                 }
-                int rc = rtl::pool_step(p.batch, n);
+                int rc = rtl::pool_set_active(p.batch, (hi + 31) / 32);
+                if (!rc) rc = rtl::pool_step(p.batch, n);
                 if (!rc && cudaEventRecord(p.done_ev, rtl::pool_stream(p.batch)) != cudaSuccess) rc = SIM_ERR_CUDA;
                 if (rc) {
                     fail_pool_jobs(p, sim_last_error());
