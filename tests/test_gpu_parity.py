@@ -147,9 +147,12 @@ def test_mid_closed_forms_at_depth(mid_text):
     assert b.peek_reg(0, names["chk_lfsr32"]) == gf2_apply(gf2_pow(galois_matrix(netgen.LFSR32_MASK), n), 1)
 
 
-def test_poke_peek_and_checkpoint(tiny_text):
+@pytest.mark.parametrize("cfg", [{}, dict(cluster_size=8, warps_per_cta=1, target_processes=8),
+                                 dict(cluster_size=2, warps_per_cta=2, target_processes=8)],
+                         ids=["grid_barrier", "one_cluster", "two_clusters"])
+def test_poke_peek_and_checkpoint(tiny_text, cfg):
     n = 200
-    nl = sim.Netlist(tiny_text, mode="lane_op", digest_capacity=1000)
+    nl = sim.Netlist(tiny_text, mode="lane_op", digest_capacity=1000, **cfg)
     b = sim.Batch(nl, 1, seed=4)
     ref = oracle.Sim(oracle.Net(text=tiny_text), seed=4, inst=0)
     b.step(n)
@@ -202,8 +205,11 @@ minit 1 5 4242
 minit 0 3 7
 end
 """
-    for mode, n_inst in (("lane_op", 1), ("lane_inst", 33)):
-        nl = sim.Netlist(text, mode=mode, digest_capacity=400, lowering=lowering)
+    cases = [("lane_op", 1, {}), ("lane_inst", 33, {})]
+    if lowering == "bytecode":      # cluster exchange runs the bytecode
+        cases.append(("lane_op", 1, dict(cluster_size=2, warps_per_cta=1, target_processes=2)))
+    for mode, n_inst, extra in cases:
+        nl = sim.Netlist(text, mode=mode, digest_capacity=400, lowering=lowering, **extra)
         b = sim.Batch(nl, n_inst, seed=1, track=[0, n_inst - 1])
         ref = oracle.Sim(oracle.Net(text=text), seed=1, inst=0)
         want = [ref.digest()]
