@@ -36,7 +36,7 @@ STATE_BYTES_MID = 6126 / 8 + 7955 * 4 + 5927 * 8
 # per-cycle exchange stays in L2 (capture: ncu --metrics dram__bytes_read.sum,
 # dram__bytes_write.sum -k regex:k_cycles_cl -s 1 -c 1 on `bench.py --no-rows
 # --steps 2 --warmup 1`)
-HEADLINE_TRAFFIC = 4.87e6 + 0.105e6
+HEADLINE_TRAFFIC = 4.85e6 + 0.100e6
 WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
             "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
             "100k cycles; persistent kernel, autotuned geometry (grid barrier, optional cluster exchange)")
