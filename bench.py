@@ -175,7 +175,8 @@ def mesh_row(stream, flush):
     from paper_2403_04714_gb300 import netgen, sim
     text = open(netgen.cached_netlist("mesh"), "rb").read()
     out = {}
-    for name, cfg in (("grid_barrier", {}), ("cluster", dict(cluster_size=2, warps_per_cta=8))):
+    for name, cfg in (("grid_barrier", dict(target_processes=1216, warps_per_cta=8)),
+                      ("cluster", dict(cluster_size=2, warps_per_cta=8))):
         try:
             nl = sim.Netlist(text, mode="lane_op", **cfg)
             b = sim.Batch(nl, 1, seed=42, stream=stream)
