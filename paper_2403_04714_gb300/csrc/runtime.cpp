@@ -157,6 +157,7 @@ namespace rtl { struct PoolExtra; void pool_extra_free(PoolExtra*); }
 
 struct sim_batch {
     sim_netlist* nl = nullptr;
+    sim_config cfg{};                      // the configuration this batch was created with
     rtl::PoolExtra* pool = nullptr;        // set for server pools
     bool generated = false;                // processes run as generated CUDA
     const void* gen_kernel[2] = {nullptr, nullptr};
@@ -223,6 +224,8 @@ struct sim_batch {
 
 namespace {
 int ensure_compiled(sim_netlist* h, int mode);
+int create_instances(sim_netlist* nl, const sim_config& cfg, uint32_t n_inst, uint64_t seed, void* cuda_stream,
+                     sim_batch** out);
 }
 
 extern "C" {
@@ -460,7 +463,7 @@ int plan_launch_gen(sim_batch* b) {
     b->prog_words = 0;
     b->smem = 0;
     // generated kernels: up to 1024 threads per CTA at 64 registers per thread
-    int warps = std::min(32, b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8);
+    int warps = std::min(32, b->cfg.warps_per_cta ? int(b->cfg.warps_per_cta) : 8);
     b->warps = warps;
     b->threads = warps * 32;
     int occ = 0;
@@ -577,8 +580,8 @@ int plan_launch(sim_batch* b) {
     if (slot_bytes > smem_cap)
         return set_err(SIM_ERR_CAPACITY, "a process needs " + std::to_string(slot_bytes) +
                                              " bytes of value slots per warp (limit " + std::to_string(smem_cap) + ")");
-    int warps = b->nl->cfg.warps_per_cta ? int(b->nl->cfg.warps_per_cta) : 8;
-    if (!b->nl->cfg.warps_per_cta && b->mode == SIM_MODE_LANE_OP)   // one process per warp, one CTA per SM
+    int warps = b->cfg.warps_per_cta ? int(b->cfg.warps_per_cta) : 8;
+    if (!b->cfg.warps_per_cta && b->mode == SIM_MODE_LANE_OP)   // one process per warp, one CTA per SM
         warps = int(std::min<uint64_t>(16, std::max<uint64_t>(1, (uint64_t(n_proc) * b->I + sms - 1) / sms)));
     while (warps > 1 && size_t(warps) * slot_bytes > smem_cap) warps /= 2;
     b->warps = warps;
@@ -779,8 +782,7 @@ uint64_t initial_digest(const sim_netlist* h) {
 }
 
 int setup_tracking(sim_batch* b, const std::vector<uint32_t>& insts) {
-    sim_netlist* h = b->nl;
-    const uint32_t cap = h->cfg.digest_capacity;
+    const uint32_t cap = b->cfg.digest_capacity;
     DevState& S = b->S;
     b->tracked = insts;
     b->h_track.assign(b->I, -1);
@@ -792,7 +794,7 @@ int setup_tracking(sim_batch* b, const std::vector<uint32_t>& insts) {
     S.n_tracked = uint32_t(insts.size());
     if (cap && !insts.empty()) {
         std::vector<uint64_t> ring(size_t(cap) * insts.size(), 0);
-        uint64_t d0 = initial_digest(h);
+        uint64_t d0 = initial_digest(b->nl);
         for (size_t k = 0; k < insts.size(); k++) ring[k] = d0;   // state 0 in slot 0
         if ((rc = upload(b->ring, ring, b->stream))) return rc;
         S.ring = b->ring.as<uint64_t>();
@@ -855,9 +857,9 @@ int clear_ring(sim_batch* b, uint64_t t0, uint64_t n) {
 
 int step_persistent(sim_batch* b, uint64_t n) {
     LaunchArgs A = base_args(b);
-    if (b->nl->cfg.phase_samples) {
-        const uint32_t want = std::min<uint64_t>(b->nl->cfg.phase_samples, n);
-        const size_t bytes = size_t(b->nl->cfg.phase_samples) * b->grid * 24;
+    if (b->cfg.phase_samples) {
+        const uint32_t want = std::min<uint64_t>(b->cfg.phase_samples, n);
+        const size_t bytes = size_t(b->cfg.phase_samples) * b->grid * 24;
         if (b->phase.n < bytes) {
             int rc = b->phase.alloc(bytes);
             if (rc) return rc;
@@ -1018,11 +1020,24 @@ void reg_addr(sim_batch* b, uint32_t par, uint32_t r, uint32_t inst, void** p, i
 extern "C" {
 
 int sim_create_instances(sim_netlist* nl, uint32_t n_inst, uint64_t seed, void* cuda_stream, sim_batch** out) {
+    if (!nl) return set_err(SIM_ERR_BADARG, "bad argument");
+    return create_instances(nl, nl->cfg, n_inst, seed, cuda_stream, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// sim_create_instances with an explicit configuration (server pools override
+// the lane mapping, kernel and digests without touching the netlist's).
+int create_instances(sim_netlist* nl, const sim_config& cfg, uint32_t n_inst, uint64_t seed, void* cuda_stream,
+                     sim_batch** out) {
     if (!nl || !out || n_inst == 0) return set_err(SIM_ERR_BADARG, "bad argument");
     *out = nullptr;
     try {
         std::unique_ptr<sim_batch> b(new sim_batch());
         b->nl = nl;
+        b->cfg = cfg;
         b->stream = static_cast<cudaStream_t>(cuda_stream);
         if (!b->stream) {     // a private stream (graph capture needs a non-legacy stream)
             CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
@@ -1030,24 +1045,24 @@ int sim_create_instances(sim_netlist* nl, uint32_t n_inst, uint64_t seed, void* 
         }
         b->n_inst = n_inst;
         b->seed = seed;
-        b->mode = nl->cfg.mode == SIM_MODE_AUTO ? (n_inst >= 32 ? SIM_MODE_LANE_INST : SIM_MODE_LANE_OP) : nl->cfg.mode;
-        b->kernel = nl->cfg.kernel;
+        b->mode = cfg.mode == SIM_MODE_AUTO ? (n_inst >= 32 ? SIM_MODE_LANE_INST : SIM_MODE_LANE_OP) : cfg.mode;
+        b->kernel = cfg.kernel;
         b->I = b->mode == SIM_MODE_LANE_INST ? (n_inst + 31) / 32 * 32 : n_inst;
-        b->timeout_ns = uint64_t(nl->cfg.timeout_ms ? nl->cfg.timeout_ms : 2000) * 1000000ULL;
+        b->timeout_ns = uint64_t(cfg.timeout_ms ? cfg.timeout_ms : 2000) * 1000000ULL;
         // lane = instance: process-major task order unless the config asks otherwise
-        b->proc_major = nl->cfg.task_order == SIM_ORDER_PROCESS_MAJOR || nl->cfg.task_order == SIM_ORDER_CTA_MAJOR ||
-                        (nl->cfg.task_order == SIM_ORDER_AUTO && b->mode == SIM_MODE_LANE_INST);
+        b->proc_major = cfg.task_order == SIM_ORDER_PROCESS_MAJOR || cfg.task_order == SIM_ORDER_CTA_MAJOR ||
+                        (cfg.task_order == SIM_ORDER_AUTO && b->mode == SIM_MODE_LANE_INST);
         // waves trade code reuse for L2 reuse of the state; measured on the
         // 4096-instance mid batch, code reuse wins (one wave of all groups)
-        b->wave_groups = nl->cfg.wave_groups;
-        b->cta_major = nl->cfg.task_order == SIM_ORDER_CTA_MAJOR;
+        b->wave_groups = cfg.wave_groups;
+        b->cta_major = cfg.task_order == SIM_ORDER_CTA_MAJOR;
         int rc;
-        if (nl->cfg.cluster_size && (n_inst != 1 || b->mode != SIM_MODE_LANE_OP))
+        if (cfg.cluster_size && (n_inst != 1 || b->mode != SIM_MODE_LANE_OP))
             return set_err(SIM_ERR_BADARG, "a netlist lowered for cluster exchange runs one instance (LANE_OP)");
         if ((rc = upload_program(b.get())) || (rc = init_state(b.get()))) return rc;
-        if (nl->cfg.cluster_size) {
+        if (cfg.cluster_size) {
             if ((rc = plan_launch_cluster(b.get()))) return rc;
-        } else if (nl->cfg.lowering == SIM_LOWER_GENERATED) {
+        } else if (cfg.lowering == SIM_LOWER_GENERATED) {
             if ((rc = ensure_loaded(nl, b->mode))) return rc;
             b->generated = true;
             b->gen_kernel[0] = reinterpret_cast<const void*>(nl->gen[b->mode].kernel[0]);
@@ -1065,6 +1080,10 @@ int sim_create_instances(sim_netlist* nl, uint32_t n_inst, uint64_t seed, void* 
         return set_err(SIM_ERR_OOM, "host allocation failed");
     }
 }
+
+}  // namespace
+
+extern "C" {
 
 void sim_batch_destroy(sim_batch* b) {
     if (!b) return;
@@ -1484,12 +1503,15 @@ size_t pool_footprint(const sim_netlist* h, uint32_t capacity) {
 
 int pool_create(sim_netlist* nl, uint32_t capacity, sim_batch** out) {
     if (!nl || !out || capacity == 0) return set_err(SIM_ERR_BADARG, "bad argument");
-    sim_config saved = nl->cfg;
-    nl->cfg.mode = SIM_MODE_LANE_INST;
-    nl->cfg.kernel = SIM_KERNEL_PER_CYCLE_GRAPH;
-    nl->cfg.digest_capacity = 0;
-    int rc = sim_create_instances(nl, capacity, 0, nullptr, out);
-    nl->cfg = saved;
+    // a pool runs lane = instance with per-cycle graphs and no digest ring,
+    // whatever the netlist was loaded for (its LANE_INST program is always
+    // there, also when the LANE_OP program was lowered for clusters)
+    sim_config cfg = nl->cfg;
+    cfg.mode = SIM_MODE_LANE_INST;
+    cfg.kernel = SIM_KERNEL_PER_CYCLE_GRAPH;
+    cfg.digest_capacity = 0;
+    cfg.cluster_size = 0;
+    int rc = create_instances(nl, cfg, capacity, 0, nullptr, out);
     if (rc) return rc;
     sim_batch* b = *out;
     std::unique_ptr<PoolExtra> x(new PoolExtra());
