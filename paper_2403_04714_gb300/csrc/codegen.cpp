@@ -208,6 +208,40 @@ struct Emitter {
 
 }  // namespace
 
+namespace {
+
+// Order in which a process's fibers are emitted: greedily the fiber that
+// uses most of the values already computed for earlier fibers (shared logic),
+// so that those values are consumed, and can die, soon after they are made;
+// ties go to the fiber with the least new work, then to the lower index.  The
+// live intermediate values of a process function set its register pressure.
+std::vector<int32_t> fiber_order(const Partition& part, size_t p, const std::vector<int32_t>& local, size_t n_local) {
+    const auto& fibs = part.procs[p];
+    std::vector<int32_t> order;
+    order.reserve(fibs.size());
+    std::vector<uint8_t> made(n_local, 0), taken(fibs.size(), 0);
+    for (size_t k = 0; k < fibs.size(); k++) {
+        size_t best = fibs.size();
+        int64_t best_shared = -1, best_new = 0;
+        for (size_t i = 0; i < fibs.size(); i++) {
+            if (taken[i]) continue;
+            int64_t shared = 0, fresh = 0;
+            for (int32_t n : part.fibers[fibs[i]].nodes) (made[local[n]] ? shared : fresh)++;
+            if (shared > best_shared || (shared == best_shared && fresh < best_new)) {
+                best = i;
+                best_shared = shared;
+                best_new = fresh;
+            }
+        }
+        taken[best] = 1;
+        order.push_back(fibs[best]);
+        for (int32_t n : part.fibers[fibs[best]].nodes) made[local[n]] = 1;
+    }
+    return order;
+}
+
+}  // namespace
+
 void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p, int mode, std::string& o) {
     std::vector<int32_t> nodes;
     for (int32_t f : part.procs[p]) nodes.insert(nodes.end(), part.fibers[f].nodes.begin(), part.fibers[f].nodes.end());
@@ -234,7 +268,7 @@ void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, s
     if (has_input) o += "    const uint64_t key = S.key[inst];\n";
     for (int32_t f : part.procs[p])
         if (part.fibers[f].mem >= 0) E.commit(part.fibers[f].mem);
-    for (int32_t f : part.procs[p]) {
+    for (int32_t f : fiber_order(part, p, E.local, nodes.size())) {
         const Fiber& fb = part.fibers[f];
         if (fb.reg >= 0) {
             E.emit_cone(nl.reg_next[fb.reg]);
