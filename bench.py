@@ -328,6 +328,24 @@ def run_cpu_baseline(path, cycles, seed=42):
     return cycles / dt, dt
 
 
+def host_cpu():
+    """The host the oracle ran on: logical cores and CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and ":" in line:
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"nproc": os.cpu_count(), "cpu": model}
+
+
 def reference_arm(args, rank):
     """The oracle, as it stands, on the host cores (the reference arm)."""
     if rank != 0:
@@ -353,7 +371,8 @@ def reference_arm(args, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "sample": sample},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                         "host": host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }))
 
@@ -488,7 +507,8 @@ def main():
         oracle.build()
         v, dt = run_cpu_baseline(path, args.cpu_cycles)
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"first {args.cpu_cycles} cycles of the mid netlist, 1 instance ({dt:.1f} s)"}
+               "sample": f"first {args.cpu_cycles} cycles of the mid netlist, 1 instance ({dt:.1f} s)",
+               "host": host_cpu()}
 
     if rank == 0:
         out = {
