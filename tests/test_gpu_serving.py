@@ -80,3 +80,15 @@ def test_admission_under_a_tight_cap(nets):
         srv.submit(b, 100_000, 1, 10)
     assert e.value.name == "SIM_ERR_ADMISSION"
     srv.close()
+
+
+def test_pool_of_a_cluster_lowered_netlist(nets):
+    # a netlist loaded for cluster exchange (one instance) still serves
+    # multi-instance jobs: pools run its lane = instance program
+    nl = sim.Netlist(nets["tiny"], mode="lane_op", cluster_size=2, warps_per_cta=2, target_processes=8)
+    srv = sim.Server(pool_slots=64, chunk_cycles=64)
+    jid = srv.submit(nl, 40, 21, 300)
+    srv.wait(jid)
+    assert srv.poll(jid)["state"] == "done"
+    assert np.array_equal(srv.digests(jid, 40), solo(nets["tiny"], 40, 21, 300))
+    srv.close()
