@@ -233,6 +233,71 @@ def prng_row(stream, per_proc=(1, 8, 64), procs=1216, cycles=2000):
     return out
 
 
+def sync_sweep_row(stream, per_proc=(1, 32, 256), procs=(38, 152, 608, 1216, 2432), cycles=2000):
+    """Sec. 4.1 synchronisation experiment as a sweep (the paper's PRNG rate
+    figure): the number of processes (warps, the GPU's counterpart of tiles)
+    grows with the number of independent xorshift fibers, fibers per process
+    held fixed; t_comm = 0, so the rate falls only through the barrier and
+    through warps sharing an SM.  Rates are normalised to the smallest grid."""
+    from paper_2403_04714_gb300 import netgen, sim
+    import numpy as np
+    out = {}
+    for k in per_proc:
+        line, base = {}, None
+        for P in procs:
+            if P * k > 400_000:        # generation alone would take tens of seconds
+                continue
+            try:
+                nl = sim.Netlist(netgen.gen_prng(P * k).to_text(), mode="lane_op", target_processes=P,
+                                 phase_samples=cycles)
+                b = sim.Batch(nl, 1, seed=1, stream=stream)
+            except sim.SimError as e:
+                line[str(P)] = {"unavailable": str(e)}
+                continue
+            b.step(cycles)
+            b.sync()
+            t = time.perf_counter()
+            b.step(cycles)
+            b.sync()
+            rate = cycles / (time.perf_counter() - t)
+            base = base or rate
+            ph = np.median(b.phase_times(cycles)[100:], axis=0)
+            line[str(P)] = {"cycles_per_s": rate, "normalised": rate / base, "compute_ns": float(ph[0]),
+                            "sync_ns": float(ph[1]), "steps": nl.info()["max_bundles"],
+                            "launch": b.launch_info()}
+            del b, nl
+        out[f"fibers_per_process_{k}"] = line
+    return out
+
+
+def mesh_weak_row(stream, flush, sides=(2, 3, 4, 5, 6)):
+    """Weak scaling of the mesh design (the paper's srN / lrN series, Sec. 6):
+    N x N blocks of 30k ops and 2k registers each, N = 2..6, one instance, the
+    plain grid-barrier kernel and the cluster exchange (2-CTA clusters, 8 warps
+    per CTA)."""
+    from paper_2403_04714_gb300 import netgen, sim
+    out = {}
+    for n in sides:
+        text = netgen.gen_mesh(1100 + n, mesh=n, ops_per_block=30_000, regs_per_block=2_000, depth=40,
+                               inputs_per_block=8).to_text()
+        r = {}
+        for kind, cfg in (("grid_barrier", dict()), ("cluster", dict(cluster_size=2, warps_per_cta=8))):
+            try:
+                nl = sim.Netlist(text, mode="lane_op", **cfg)
+                b = sim.Batch(nl, 1, seed=42, stream=stream)
+            except sim.SimError as e:
+                r[kind] = {"unavailable": str(e)}
+                continue
+            ms, lk = time_steps(b, stream, 3, 1, 1000, flush)
+            i = nl.info()
+            r[kind] = {"cycles_per_s": 3000 / (sum(ms) / 1000.0), "processes": i["n_processes"],
+                       "steps": i["max_bundles"], "launch": b.launch_info()}
+            r["ops"], r["registers"] = i["n_ops"], i["n_regs"]
+            del b, nl
+        out[f"{n}x{n}"] = r
+    return out
+
+
 def cluster_row(stream, flush):
     """Cluster exchange against the plain grid-barrier kernel, one instance: a
     design that fits one 16-CTA cluster synchronises with the cluster barrier
@@ -389,7 +454,8 @@ def main():
     ap.add_argument("--batched-cycles", type=int, default=200)
     ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
     ap.add_argument("--rows", default="single,batched,mesh,cluster,served",
-                    help="comma list of extra rows: single, batched, mesh, cluster, served")
+                    help="comma list of extra rows: single, batched, mesh, cluster, served; "
+                         "opt-in sweeps: sync_sweep, mesh_weak")
     args = ap.parse_args()
     rank, world, local, dist = (0, 1, 0, None)
     if args.impl == "reference":
@@ -496,6 +562,10 @@ def main():
             rows["cluster_exchange"] = cluster_row(stream, flush)
         if "served" in want:
             rows["served"] = served_row()
+        if "sync_sweep" in want:
+            rows["sync_sweep"] = sync_sweep_row(stream)
+        if "mesh_weak" in want:
+            rows["mesh_weak"] = mesh_weak_row(stream, flush)
 
     # ---- measured integer issue rate (the ALU roof, next to the derived one) ---
     int_peak = sim.measure_int_peak(1 << 14)
