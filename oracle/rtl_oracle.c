@@ -28,6 +28,23 @@
  *     the highest-numbered port wins on an address conflict;
  *   - register next values are truncated or zero-extended to the register width.
  *
+ * Clocks (paper Sec. 5, limitations: one top-level clock plus any number of
+ * gated or divided clocks).  Our reading, in Verilog's event order:
+ *   - `gate r e`: register r's clock is gated by node e; at an edge of its
+ *     clock r takes its next value only if e is nonzero (e is evaluated
+ *     together with r's next value);
+ *   - `clock r d`: register r is clocked by the rising edge of the 1-bit
+ *     register d (a divided clock).  d changes at its own clock edge, so the
+ *     edge of r's clock comes after d's domain has committed: r's next value
+ *     (and gate) are evaluated on the state *after* that commit, i.e. r
+ *     samples the new values of the registers of earlier domains.
+ *   One top-clock cycle therefore runs in phases: phase 0 evaluates every
+ *   node and commits the top-clock registers and the memory writes; phase k
+ *   re-evaluates every node on the state now and commits the registers whose
+ *   clock register (of phase k-1) went from 0 at the start of the cycle to 1.
+ *   Memory reads in the cone of a register on a divided clock are rejected
+ *   (write ports are on the top clock).
+ *
  * Stimulus: each input value is drawn from SplitMix64 (Steele, Lea and Flood,
  * "Fast splittable pseudorandom number generators", OOPSLA 2014), used as a
  * counter-based generator: output number n of a SplitMix64 stream seeded
@@ -73,6 +90,10 @@ typedef struct {
     int *reg_w;
     uint64_t *reg_init;
     int64_t *reg_next;
+    int64_t *reg_gate;    /* gate node of each register, or -1 */
+    int64_t *reg_clk;     /* clock register of each register, or -1 (top clock) */
+    int *reg_depth;       /* 0 on the top clock, 1 + depth of the clock register */
+    int max_depth;
     int *mem_lg, *mem_w;
     uint64_t **mem_init;  /* per memory, depth words */
     onode *node;
@@ -91,6 +112,7 @@ typedef struct {
     uint64_t cycle;
     uint64_t *reg;        /* current register values */
     uint64_t *reg_nx;     /* scratch for next values */
+    uint64_t *reg_start;  /* register values at the start of the cycle */
     uint64_t **mem;
     uint64_t *val;        /* node values of the cycle being evaluated */
     uint64_t *in_val;
@@ -246,11 +268,15 @@ static int parse_text(onet *n, char *text, char *err, size_t errlen)
                 GROW(n->reg_w, n->n_reg, c);
                 c = cap_reg; GROW(n->reg_init, n->n_reg, c);
                 c = cap_reg; GROW(n->reg_next, n->n_reg, c);
+                c = cap_reg; GROW(n->reg_gate, n->n_reg, c);
+                c = cap_reg; GROW(n->reg_clk, n->n_reg, c);
                 cap_reg = c;
             }
             n->reg_w[n->n_reg] = (int)w;
             n->reg_init[n->n_reg] = init;
             n->reg_next[n->n_reg] = -1;
+            n->reg_gate[n->n_reg] = -1;
+            n->reg_clk[n->n_reg] = -1;
             n->n_reg++;
         } else if (!strcmp(tok[0], "mem")) {
             int64_t lg, w;
@@ -293,6 +319,15 @@ static int parse_text(onet *n, char *text, char *err, size_t errlen)
             if (r < 0 || r >= n->n_reg) return fail(err, errlen, "line %d: next of unknown register", line_no);
             if (n->reg_next[r] >= 0) return fail(err, errlen, "line %d: register %lld has two next", line_no, (long long)r);
             n->reg_next[r] = x;
+        } else if (!strcmp(tok[0], "gate") || !strcmp(tok[0], "clock")) {
+            int64_t r, x;
+            int is_gate = !strcmp(tok[0], "gate");
+            if (nt != 3 || parse_i64(tok[1], &r) || parse_i64(tok[2], &x))
+                return fail(err, errlen, "line %d: bad %s", line_no, tok[0]);
+            if (r < 0 || r >= n->n_reg) return fail(err, errlen, "line %d: %s of unknown register", line_no, tok[0]);
+            int64_t *slot = is_gate ? &n->reg_gate[r] : &n->reg_clk[r];
+            if (*slot >= 0) return fail(err, errlen, "line %d: register %lld has two %s items", line_no, (long long)r, tok[0]);
+            *slot = x;
         } else if (!strcmp(tok[0], "wport")) {
             int64_t v[4];
             if (nt != 5) return fail(err, errlen, "line %d: bad wport", line_no);
@@ -385,6 +420,22 @@ static int check_and_order(onet *n, char *err, size_t errlen)
         if (n->reg_w[r] < 1 || n->reg_w[r] > 64) return fail(err, errlen, "register %d: width out of range", r);
         if (n->reg_next[r] < 0 || n->reg_next[r] >= N) return fail(err, errlen, "register %d: missing or bad next", r);
         n->reg_init[r] &= mask_of(n->reg_w[r]);
+        if (n->reg_gate[r] >= N) return fail(err, errlen, "register %d: bad gate node", r);
+        if (n->reg_clk[r] >= 0) {
+            int64_t d = n->reg_clk[r];
+            if (d >= n->n_reg || d == r) return fail(err, errlen, "register %d: bad clock register", r);
+            if (n->reg_w[d] != 1) return fail(err, errlen, "register %d: clock register must be 1 bit", r);
+        }
+    }
+    /* depth of each register's clock: the length of its chain of clock registers */
+    n->reg_depth = calloc((size_t)n->n_reg + 1, sizeof(int));
+    n->max_depth = 0;
+    for (int r = 0; r < n->n_reg; r++) {
+        int depth = 0;
+        for (int64_t q = n->reg_clk[r]; q >= 0; q = n->reg_clk[q])
+            if (++depth > n->n_reg) return fail(err, errlen, "register %d: loop of clock registers", r);
+        n->reg_depth[r] = depth;
+        if (depth > n->max_depth) n->max_depth = depth;
     }
     for (int p = 0; p < n->n_wport; p++) {
         if (n->wp_mem[p] < 0 || n->wp_mem[p] >= n->n_mem) return fail(err, errlen, "wport %d: bad memory", p);
@@ -449,6 +500,29 @@ static int check_and_order(onet *n, char *err, size_t errlen)
     }
     free(indeg); free(cnt); free(users); free(fillp);
     if (tail != N) return fail(err, errlen, "combinational loop");
+    /* no memory read in the cone of a register on a divided clock */
+    if (n->max_depth > 0) {
+        int64_t *seen = calloc((size_t)N + 1, sizeof(int64_t));
+        int64_t *stack = malloc(sizeof(int64_t) * (size_t)(N + 1));
+        for (int r = 0; r < n->n_reg; r++) {
+            if (n->reg_depth[r] == 0) continue;
+            int64_t sp = 0;
+            stack[sp++] = n->reg_next[r];
+            if (n->reg_gate[r] >= 0) stack[sp++] = n->reg_gate[r];
+            while (sp > 0) {
+                int64_t i = stack[--sp];
+                if (seen[i] == r + 1) continue;
+                seen[i] = r + 1;
+                if (n->node[i].kind == K_MEMRD) {
+                    free(seen); free(stack);
+                    return fail(err, errlen, "register %d: memory read under a divided clock", r);
+                }
+                for (int k = 0; k < 3; k++)
+                    if (operand_bits(n->node[i].kind) >> k & 1) stack[sp++] = n->node[i].arg[k];
+            }
+        }
+        free(seen); free(stack);
+    }
     n->pos = malloc(sizeof(int64_t) * (size_t)(N + 1));
     n->step = malloc(sizeof(onode) * (size_t)(N + 1));
     for (int64_t j = 0; j < N; j++) n->pos[n->order[j]] = j;
@@ -497,6 +571,7 @@ void orc_net_free(onet *n)
 {
     if (!n) return;
     free(n->in_w); free(n->reg_w); free(n->reg_init); free(n->reg_next);
+    free(n->reg_gate); free(n->reg_clk); free(n->reg_depth);
     if (n->mem_init)
         for (int m = 0; m < n->n_mem; m++) free(n->mem_init[m]);
     free(n->mem_init); free(n->mem_lg); free(n->mem_w);
@@ -532,6 +607,7 @@ osim *orc_sim_new(const onet *n, uint64_t seed, uint64_t inst)
     s->net = n;
     s->reg = calloc((size_t)n->n_reg + 1, sizeof(uint64_t));
     s->reg_nx = calloc((size_t)n->n_reg + 1, sizeof(uint64_t));
+    s->reg_start = calloc((size_t)n->n_reg + 1, sizeof(uint64_t));
     s->mem = calloc((size_t)n->n_mem + 1, sizeof(uint64_t *));
     for (int m = 0; m < n->n_mem; m++) s->mem[m] = calloc((size_t)1 << n->mem_lg[m], sizeof(uint64_t));
     s->val = calloc((size_t)n->n_node + 1, sizeof(uint64_t));
@@ -546,7 +622,7 @@ void orc_sim_free(osim *s)
 {
     if (!s) return;
     for (int m = 0; m < s->net->n_mem; m++) free(s->mem[m]);
-    free(s->mem); free(s->reg); free(s->reg_nx); free(s->val); free(s->in_val);
+    free(s->mem); free(s->reg); free(s->reg_nx); free(s->reg_start); free(s->val); free(s->in_val);
     free(s->in_hold); free(s->held);
     free(s);
 }
@@ -565,16 +641,11 @@ uint64_t orc_sim_digest(const osim *s)
     return d;
 }
 
-/* One simulated clock cycle: S_t -> S_{t+1} (paper Sec. 3.2). */
-static void step_once(osim *s)
+/* Every node in topological order from the current state and the inputs of
+ * this cycle; s->val[j] is the value of the node at evaluation position j. */
+static void eval_nodes(osim *s)
 {
     const onet *n = s->net;
-    /* (1) inputs of this cycle: held value, else the stimulus */
-    for (int k = 0; k < n->n_in; k++)
-        s->in_val[k] = s->held[k] ? (s->in_hold[k] & mask_of(n->in_w[k]))
-                                  : (splitmix_nth(s->key, s->cycle * (uint64_t)n->n_in + (uint64_t)k + 1) & mask_of(n->in_w[k]));
-    /* (2) every node in topological order, from current values only;
-     * s->val[j] is the value of the node at evaluation position j */
     for (int64_t j = 0; j < n->n_node; j++) {
         const onode *d = &n->step[j];
         uint64_t v;
@@ -601,8 +672,31 @@ static void step_once(osim *s)
         }
         s->val[j] = v;
     }
-    /* (3) register next values (resize to register width), then commit */
-    for (int r = 0; r < n->n_reg; r++) s->reg_nx[r] = s->val[n->pos[n->reg_next[r]]] & mask_of(n->reg_w[r]);
+}
+
+/* Next value of register r from the node values just evaluated: its next
+ * node resized to its width, or its current value when its gate is 0. */
+static uint64_t reg_next_value(const osim *s, int r)
+{
+    const onet *n = s->net;
+    if (n->reg_gate[r] >= 0 && s->val[n->pos[n->reg_gate[r]]] == 0) return s->reg[r];
+    return s->val[n->pos[n->reg_next[r]]] & mask_of(n->reg_w[r]);
+}
+
+/* One simulated clock cycle: S_t -> S_{t+1} (paper Sec. 3.2). */
+static void step_once(osim *s)
+{
+    const onet *n = s->net;
+    /* (1) inputs of this cycle: held value, else the stimulus */
+    for (int k = 0; k < n->n_in; k++)
+        s->in_val[k] = s->held[k] ? (s->in_hold[k] & mask_of(n->in_w[k]))
+                                  : (splitmix_nth(s->key, s->cycle * (uint64_t)n->n_in + (uint64_t)k + 1) & mask_of(n->in_w[k]));
+    /* (2) every node from the current values only */
+    eval_nodes(s);
+    if (n->max_depth > 0) memcpy(s->reg_start, s->reg, sizeof(uint64_t) * (size_t)n->n_reg);
+    /* (3) top-clock registers take their next values (resized), then commit */
+    for (int r = 0; r < n->n_reg; r++)
+        s->reg_nx[r] = n->reg_depth[r] == 0 ? reg_next_value(s, r) : s->reg[r];
     memcpy(s->reg, s->reg_nx, sizeof(uint64_t) * (size_t)n->n_reg);
     /* (4) memory writes in ascending port order (highest port wins) */
     for (int p = 0; p < n->n_wport; p++) {
@@ -611,6 +705,20 @@ static void step_once(osim *s)
             uint64_t a = s->val[n->pos[n->wp_addr[p]]] & ((1ULL << n->mem_lg[m]) - 1);
             s->mem[m][a] = s->val[n->pos[n->wp_data[p]]] & mask_of(n->mem_w[m]);
         }
+    }
+    /* (5) divided clocks, one phase per depth: re-evaluate on the state after
+     * the previous phase's commit; a register whose clock register rose
+     * (0 at the start of the cycle, 1 now) takes its next value */
+    for (int depth = 1; depth <= n->max_depth; depth++) {
+        eval_nodes(s);
+        for (int r = 0; r < n->n_reg; r++) {
+            if (n->reg_depth[r] != depth) continue;
+            int64_t d = n->reg_clk[r];
+            int rose = s->reg_start[d] == 0 && s->reg[d] != 0;
+            s->reg_nx[r] = rose ? reg_next_value(s, r) : s->reg[r];
+        }
+        for (int r = 0; r < n->n_reg; r++)
+            if (n->reg_depth[r] == depth) s->reg[r] = s->reg_nx[r];
     }
     s->cycle++;
 }

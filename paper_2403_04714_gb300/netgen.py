@@ -22,6 +22,10 @@ File format (`rtlnet 1`), one item per line, `#` starts a comment:
     n    <op> <width> <args...>         node i (counts `n` lines from 0)
     next <r> <node>                     next-state node of register r
     wport <m> <en> <addr> <data>        write port p of memory m (p counts `wport` lines)
+    gate <r> <node>                     register r's clock is gated by node (optional)
+    clock <r> <d>                       register r is clocked by the rising edge of the
+                                        1-bit register d, a divided clock (optional;
+                                        default: the top-level clock)
     minit <m> <addr> <value>            initial memory word (default 0)
     end
 
@@ -57,6 +61,8 @@ class Netlist:
     nodes: list = field(default_factory=list)    # (op, width, args tuple)
     wports: list = field(default_factory=list)   # (mem, en, addr, data)
     minit: list = field(default_factory=list)    # (mem, addr, value)
+    gates: dict = field(default_factory=dict)    # register -> gate node
+    clocks: dict = field(default_factory=dict)   # register -> clock register
 
     # -- construction helpers -------------------------------------------------
     def add_input(self, width, name=""):
@@ -104,6 +110,10 @@ class Netlist:
             w(f"next {r} {nxt}\n")
         for m, en, addr, data in self.wports:
             w(f"wport {m} {en} {addr} {data}\n")
+        for r, g in sorted(self.gates.items()):
+            w(f"gate {r} {g}\n")
+        for r, d in sorted(self.clocks.items()):
+            w(f"clock {r} {d}\n")
         for m, a, v in self.minit:
             w(f"minit {m} {a} {v}\n")
         w("end\n")
@@ -573,6 +583,45 @@ def gen_prng(n_fibers: int, seed: int = 5) -> Netlist:
         for sh, kind in ((13, "shl"), (7, "shr"), (17, "shl")):
             x = nl.node("xor", 64, x, nl.node(kind, 64, x, nl.node("const", 7, sh)))
         nl.set_next(r, x)
+    return nl
+
+
+def gen_clocked(seed=1004, n_ops=2_000, n_regs=64, depth=20, n_inputs=8, gated_frac=0.25,
+                divided_frac=0.25) -> Netlist:
+    """A design with one top-level clock, a divide-by-2 and a divide-by-4
+    clock (toggle registers, the second clocked by the first) and gated
+    clocks: random logic like `gen_flat`, then a share of its registers moved
+    to the divided clocks and a share gated by a 1-bit signal of the logic.
+    Check registers with closed forms: a counter on each divided clock, a
+    register on the divide-by-2 clock sampling a top-clock counter, and a
+    counter gated by bit 0 of the 32-bit LFSR."""
+    nl = gen_flat(seed, n_ops, n_regs, depth, n_inputs)      # includes the check blocks
+    rng = random.Random(seed + 1)
+    reg_ids = list(range(n_regs))
+    chk = {name[len("chk_"):]: nl.reg_index(name) for name in ("chk_counter16", "chk_lfsr32")}
+    div2 = nl.add_reg(1, 0, "clk_div2")
+    nl.set_next(div2, nl.node("xor", 1, nl.node("reg", 1, div2), nl.node("const", 1, 1)))
+    div4 = nl.add_reg(1, 0, "clk_div4")
+    nl.set_next(div4, nl.node("xor", 1, nl.node("reg", 1, div4), nl.node("const", 1, 1)))
+    nl.clocks[div4] = div2
+    for name, clk in (("cnt_div2", div2), ("cnt_div4", div4)):
+        c = nl.add_reg(16, 0, name)
+        nl.set_next(c, nl.node("add", 16, nl.node("reg", 16, c), nl.node("const", 16, 1)))
+        nl.clocks[c] = clk
+    smp = nl.add_reg(16, 0, "sample_div2")          # samples the top-clock counter
+    nl.set_next(smp, nl.node("reg", 16, chk["counter16"]))
+    nl.clocks[smp] = div2
+    gc = nl.add_reg(16, 0, "cnt_gated")             # counts cycles with LFSR bit 0 set
+    nl.set_next(gc, nl.node("add", 16, nl.node("reg", 16, gc), nl.node("const", 16, 1)))
+    nl.gates[gc] = nl.node("slice", 1, nl.node("reg", 32, chk["lfsr32"]), 0)
+    # random logic registers onto the divided and gated clocks
+    bits = [i for i, (op, w, _) in enumerate(nl.nodes) if w == 1 and op != "memrd"]
+    for r in reg_ids:
+        u = rng.random()
+        if u < divided_frac:
+            nl.clocks[r] = rng.choice((div2, div4))
+        if rng.random() < gated_frac:
+            nl.gates[r] = rng.choice(bits)
     return nl
 
 
