@@ -24,6 +24,16 @@
  * drawn (or held), all nodes are evaluated from current register and memory
  * values, registers take their next-state values, then memory write ports
  * apply in ascending port order (the highest port wins an address).
+ *
+ * Clocks (paper Sec. 5, limitations: one top-level clock plus gated or
+ * divided ones): `gate r e` lets register r take its next value only in
+ * cycles where node e is nonzero; `clock r d` puts register r on the rising
+ * edge of the 1-bit register d, which comes after d's own update, so r's next
+ * value and gate see the registers of earlier clock domains already updated
+ * in that cycle.  The loader lowers both to single-clock next-value logic
+ * (the reported op count includes it); a memory read in the cone of a
+ * register on a divided clock, a loop of clock registers or a clock register
+ * wider than one bit is a PARSE or WIDTH error.
  */
 #ifndef GB300_RTLSIM_SIM_H
 #define GB300_RTLSIM_SIM_H

@@ -77,127 +77,10 @@ inline uint64_t mask_w(int w) { return w >= 64 ? ~0ULL : ((1ULL << w) - 1); }
 
 }  // namespace
 
-int parse_netlist(const char* text, size_t len, Netlist& nl, std::string& err) {
-    Cursor cur{text, text + len};
-    const char* tok[8];
-    int tl[8];
-    bool header = false, ended = false;
-    std::vector<std::pair<int32_t, int32_t>> nexts;
-    char msg[256];
-    auto fail = [&](int code, const char* what) {
-        snprintf(msg, sizeof msg, "line %ld: %s", cur.line, what);
-        err = msg;
-        return code;
-    };
-    while (cur.p < cur.end) {
-        int nt = split_line(cur, tok, tl, 8);
-        long line = cur.line++;
-        (void)line;
-        if (nt == 0) continue;
-        if (ended) return fail(SIM_ERR_PARSE, "content after end");
-        if (nt > 8) return fail(SIM_ERR_PARSE, "too many fields");
-        if (!header) {
-            if (nt != 2 || !tok_eq(tok[0], tl[0], "rtlnet") || !tok_eq(tok[1], tl[1], "1"))
-                return fail(SIM_ERR_PARSE, "expected 'rtlnet 1'");
-            header = true;
-            continue;
-        }
-        const char* k = tok[0];
-        int kl = tl[0];
-        if (tok_eq(k, kl, "n")) {
-            Node nd;
-            int32_t w;
-            if (nt < 3 || !tok_i32(tok[2], tl[2], w)) return fail(SIM_ERR_PARSE, "bad node");
-            int op = -1;
-            for (int i = 0; i < OP_COUNT; i++)
-                if (tok_eq(tok[1], tl[1], kOpNames[i])) op = i;
-            if (op < 0) return fail(SIM_ERR_PARSE, "unknown op");
-            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "node width out of range");
-            nd.op = uint8_t(op);
-            nd.w = uint8_t(w);
-            int want = op == OP_MUX ? 3 : (op == OP_INPUT || op == OP_REG || op == OP_CONST) ? 1 : 2;
-            if (nt != 3 + want) return fail(SIM_ERR_PARSE, "wrong operand count");
-            if (op == OP_CONST) {
-                if (!tok_u64(tok[3], tl[3], nd.k)) return fail(SIM_ERR_PARSE, "bad constant");
-                nd.k &= mask_w(w);
-            } else {
-                int32_t v[3] = {-1, -1, -1};
-                for (int i = 0; i < want; i++)
-                    if (!tok_i32(tok[3 + i], tl[3 + i], v[i])) return fail(SIM_ERR_PARSE, "bad operand");
-                nd.a = v[0];
-                nd.b = v[1];
-                nd.c = v[2];
-            }
-            nl.nodes.push_back(nd);
-        } else if (tok_eq(k, kl, "in")) {
-            int32_t w;
-            if (nt < 2 || !tok_i32(tok[1], tl[1], w)) return fail(SIM_ERR_PARSE, "bad in");
-            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "input width out of range");
-            nl.in_w.push_back(uint8_t(w));
-        } else if (tok_eq(k, kl, "reg")) {
-            int32_t w;
-            uint64_t init;
-            if (nt < 3 || !tok_i32(tok[1], tl[1], w) || !tok_u64(tok[2], tl[2], init))
-                return fail(SIM_ERR_PARSE, "bad reg");
-            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "register width out of range");
-            nl.reg_w.push_back(uint8_t(w));
-            nl.reg_init.push_back(init & mask_w(w));
-            nl.reg_next.push_back(-1);
-        } else if (tok_eq(k, kl, "mem")) {
-            int32_t lg, w;
-            if (nt < 3 || !tok_i32(tok[1], tl[1], lg) || !tok_i32(tok[2], tl[2], w))
-                return fail(SIM_ERR_PARSE, "bad mem");
-            if (lg > 24) return fail(SIM_ERR_WIDTH, "memory depth out of range");
-            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "memory width out of range");
-            nl.mem_lg.push_back(uint8_t(lg));
-            nl.mem_w.push_back(uint8_t(w));
-            nl.mem_init.emplace_back();
-        } else if (tok_eq(k, kl, "next")) {
-            int32_t r, x;
-            if (nt != 3 || !tok_i32(tok[1], tl[1], r) || !tok_i32(tok[2], tl[2], x))
-                return fail(SIM_ERR_PARSE, "bad next");
-            nexts.emplace_back(r, x);
-        } else if (tok_eq(k, kl, "wport")) {
-            int32_t v[4];
-            if (nt != 5) return fail(SIM_ERR_PARSE, "bad wport");
-            for (int i = 0; i < 4; i++)
-                if (!tok_i32(tok[1 + i], tl[1 + i], v[i])) return fail(SIM_ERR_PARSE, "bad wport");
-            nl.wports.push_back({v[0], v[1], v[2], v[3]});
-        } else if (tok_eq(k, kl, "minit")) {
-            int32_t m;
-            uint64_t a, v;
-            if (nt != 4 || !tok_i32(tok[1], tl[1], m) || !tok_u64(tok[2], tl[2], a) || !tok_u64(tok[3], tl[3], v))
-                return fail(SIM_ERR_PARSE, "bad minit");
-            if (m >= int32_t(nl.mem_lg.size()) || a >= (1ULL << nl.mem_lg[m]))
-                return fail(SIM_ERR_PARSE, "minit out of range");
-            nl.mem_init[m].push_back({uint32_t(a), v & mask_w(nl.mem_w[m])});
-        } else if (tok_eq(k, kl, "end")) {
-            ended = true;
-        } else {
-            return fail(SIM_ERR_PARSE, "unknown item");
-        }
-    }
-    if (!header) { err = "missing 'rtlnet 1' header"; return SIM_ERR_PARSE; }
-    if (!ended) { err = "missing 'end'"; return SIM_ERR_PARSE; }
-
-    // ---- structural checks ------------------------------------------------
+// Node checks, op count, and the levels of a Kahn order (longest path from
+// a leaf); a node left out of the order lies on a combinational loop.
+static int check_graph(Netlist& nl, std::string& err) {
     const int32_t N = int32_t(nl.nodes.size());
-    for (auto& [r, x] : nexts) {
-        if (r < 0 || r >= int32_t(nl.reg_w.size())) { err = "next of unknown register"; return SIM_ERR_PARSE; }
-        if (nl.reg_next[r] >= 0) { err = "register has two next nodes"; return SIM_ERR_PARSE; }
-        if (x < 0 || x >= N) { err = "next node out of range"; return SIM_ERR_PARSE; }
-        nl.reg_next[r] = x;
-    }
-    for (size_t r = 0; r < nl.reg_next.size(); r++)
-        if (nl.reg_next[r] < 0) { err = "register " + std::to_string(r) + " has no next node"; return SIM_ERR_PARSE; }
-    for (auto& wp : nl.wports)
-        if (wp.mem < 0 || wp.mem >= int32_t(nl.mem_lg.size()) || wp.en >= N || wp.addr >= N || wp.data >= N) {
-            err = "write port out of range";
-            return SIM_ERR_PARSE;
-        }
-    nl.mem_ports.assign(nl.mem_lg.size(), {});
-    for (size_t p = 0; p < nl.wports.size(); p++) nl.mem_ports[nl.wports[p].mem].push_back(int32_t(p));
-
     std::vector<int32_t> indeg(N, 0);
     nl.n_ops = 0;
     for (int32_t i = 0; i < N; i++) {
@@ -272,6 +155,286 @@ int parse_netlist(const char* text, size_t len, Netlist& nl, std::string& err) {
     }
     if (int32_t(q.size()) != N) { err = "combinational loop"; return SIM_ERR_COMB_LOOP; }
     return SIM_OK;
+}
+
+// Gated and divided clocks (Sec. 5, limitations: one top-level clock plus any
+// number of gated or divided ones), lowered to a single clock so that the
+// partitioner, the lowerings and the kernels see a plain netlist.
+//
+// Reading, in Verilog's event order: a register with `gate r e` takes its
+// next value at an edge of its clock only when e is nonzero; a register with
+// `clock r d` is clocked by the rising edge of the 1-bit register d, which
+// comes after d's own domain has updated, so its next value and gate see the
+// state after that update.  With depth(r) = length of r's chain of clock
+// registers, the value a register q holds when domain k evaluates is
+//     q's value after its own edge, if depth(q) < k;   q's current value otherwise,
+// and q's value after its own edge is
+//     U(q) = fire(q) ? (gate(q) != 0 ? next(q) : q) : q,
+//     fire(q) = 1 on the top clock,  (d == 0) & U(d) for clock register d,
+// with next(q) and gate(q) evaluated in q's own domain.  Everything is then a
+// function of the state at the start of the cycle: each register's next node
+// becomes U(q), built from copies of the cones it reads in its domain (a copy
+// replaces each read of an earlier domain's register by that register's U).
+// A memory read in a divided domain is rejected (write ports are on the top
+// clock, and their data would have to be forwarded).
+static int lower_clocks(Netlist& nl, const std::vector<std::pair<int32_t, int32_t>>& gate_items,
+                        const std::vector<std::pair<int32_t, int32_t>>& clock_items, std::string& err) {
+    const int32_t R = int32_t(nl.reg_w.size());
+    const int32_t N0 = int32_t(nl.nodes.size());
+    std::vector<int32_t> gate(R, -1), clk(R, -1), depth(R, 0);
+    for (auto& [r, x] : gate_items) {
+        if (r < 0 || r >= R) { err = "gate of unknown register"; return SIM_ERR_PARSE; }
+        if (gate[r] >= 0) { err = "register " + std::to_string(r) + " has two gate items"; return SIM_ERR_PARSE; }
+        if (x < 0 || x >= N0) { err = "gate node out of range"; return SIM_ERR_PARSE; }
+        gate[r] = x;
+    }
+    for (auto& [r, d] : clock_items) {
+        if (r < 0 || r >= R) { err = "clock of unknown register"; return SIM_ERR_PARSE; }
+        if (clk[r] >= 0) { err = "register " + std::to_string(r) + " has two clock items"; return SIM_ERR_PARSE; }
+        if (d < 0 || d >= R || d == r) { err = "bad clock register"; return SIM_ERR_PARSE; }
+        if (nl.reg_w[d] != 1) { err = "clock register must be 1 bit"; return SIM_ERR_WIDTH; }
+        clk[r] = d;
+    }
+    int32_t max_depth = 0;
+    for (int32_t r = 0; r < R; r++) {
+        int32_t dp = 0;
+        for (int32_t q = clk[r]; q >= 0; q = clk[q])
+            if (++dp > R) { err = "loop of clock registers"; return SIM_ERR_PARSE; }
+        depth[r] = dp;
+        max_depth = std::max(max_depth, dp);
+    }
+    auto add = [&](uint8_t op, int w, int32_t a, int32_t b = -1, int32_t c = -1, uint64_t k = 0) {
+        Node nd;
+        nd.op = op;
+        nd.w = uint8_t(w);
+        nd.a = a;
+        nd.b = b;
+        nd.c = c;
+        nd.k = k;
+        nl.nodes.push_back(nd);
+        return int32_t(nl.nodes.size() - 1);
+    };
+    std::vector<int32_t> reg_read(R, -1), after(R, -1), rose(R, -1);
+    auto read_of = [&](int32_t r) {
+        if (reg_read[r] < 0) reg_read[r] = add(OP_REG, nl.reg_w[r], r);
+        return reg_read[r];
+    };
+    int32_t zero1 = -1;
+    // copy of the cone of `root` as domain k sees it (k = 0: the graph itself)
+    std::vector<std::vector<int32_t>> memo(size_t(max_depth) + 1);
+    std::vector<int32_t> stack;
+    auto in_domain = [&](int32_t k, int32_t root, int32_t& out) -> int {
+        if (k == 0) { out = root; return SIM_OK; }
+        std::vector<int32_t>& m = memo[k];
+        if (m.empty()) m.assign(N0, -1);
+        stack.assign(1, root);
+        while (!stack.empty()) {
+            const int32_t i = stack.back();
+            if (m[i] >= 0) { stack.pop_back(); continue; }
+            const Node nd = nl.nodes[i];
+            if (nd.op == OP_MEMRD) {
+                err = "memory read under a divided clock (node " + std::to_string(i) + ")";
+                return SIM_ERR_PARSE;
+            }
+            if (nd.op == OP_REG) {
+                m[i] = depth[nd.a] < k ? after[nd.a] : i;
+                stack.pop_back();
+                continue;
+            }
+            if (nd.op == OP_INPUT || nd.op == OP_CONST) { m[i] = i; stack.pop_back(); continue; }
+            int32_t ops[3] = {nd.a, nd.op == OP_SLICE ? -1 : nd.b, nd.op == OP_MUX ? nd.c : -1};
+            bool ready = true;
+            for (int32_t o : ops)
+                if (o >= 0 && m[o] < 0) { stack.push_back(o); ready = false; }
+            if (!ready) continue;
+            stack.pop_back();
+            bool same = true;
+            for (int32_t o : ops) same = same && (o < 0 || m[o] == o);
+            if (same) { m[i] = i; continue; }
+            Node cp = nd;
+            cp.a = m[nd.a];
+            if (nd.op != OP_SLICE) cp.b = m[nd.b];
+            if (nd.op == OP_MUX) cp.c = m[nd.c];
+            nl.nodes.push_back(cp);
+            m[i] = int32_t(nl.nodes.size() - 1);
+        }
+        out = m[root];
+        return SIM_OK;
+    };
+    for (int32_t k = 0; k <= max_depth; k++) {
+        for (int32_t r = 0; r < R; r++) {
+            if (depth[r] != k) continue;
+            const int w = nl.reg_w[r];
+            if (k == 0 && gate[r] < 0) {
+                // unchanged register; its value after the edge, at its own width
+                const int32_t nx = nl.reg_next[r];
+                const int wn = nl.nodes[nx].w;
+                after[r] = wn == w ? nx : wn > w ? add(OP_SLICE, w, nx, 0)
+                                                 : add(OP_OR, w, nx, add(OP_CONST, w, -1, -1, -1, 0));
+                continue;
+            }
+            int32_t nx, sel = -1;
+            int rc = in_domain(k, nl.reg_next[r], nx);
+            if (rc) return rc;
+            if (k > 0) {
+                const int32_t d = clk[r];
+                if (rose[d] < 0) {
+                    if (zero1 < 0) zero1 = add(OP_CONST, 1, -1, -1, -1, 0);
+                    rose[d] = add(OP_AND, 1, add(OP_EQ, 1, read_of(d), zero1), after[d]);
+                }
+                sel = rose[d];
+            }
+            if (gate[r] >= 0) {
+                int32_t g;
+                rc = in_domain(k, gate[r], g);
+                if (rc) return rc;
+                if (sel < 0) {
+                    sel = g;
+                } else {
+                    if (zero1 < 0) zero1 = add(OP_CONST, 1, -1, -1, -1, 0);
+                    sel = add(OP_MUX, 1, g, sel, zero1);
+                }
+            }
+            after[r] = add(OP_MUX, w, sel, nx, read_of(r));
+        }
+    }
+    for (int32_t r = 0; r < R; r++)
+        if (depth[r] > 0 || gate[r] >= 0) nl.reg_next[r] = after[r];
+    return SIM_OK;
+}
+
+int parse_netlist(const char* text, size_t len, Netlist& nl, std::string& err) {
+    Cursor cur{text, text + len};
+    const char* tok[8];
+    int tl[8];
+    bool header = false, ended = false;
+    std::vector<std::pair<int32_t, int32_t>> nexts, gate_items, clock_items;
+    char msg[256];
+    auto fail = [&](int code, const char* what) {
+        snprintf(msg, sizeof msg, "line %ld: %s", cur.line, what);
+        err = msg;
+        return code;
+    };
+    while (cur.p < cur.end) {
+        int nt = split_line(cur, tok, tl, 8);
+        long line = cur.line++;
+        (void)line;
+        if (nt == 0) continue;
+        if (ended) return fail(SIM_ERR_PARSE, "content after end");
+        if (nt > 8) return fail(SIM_ERR_PARSE, "too many fields");
+        if (!header) {
+            if (nt != 2 || !tok_eq(tok[0], tl[0], "rtlnet") || !tok_eq(tok[1], tl[1], "1"))
+                return fail(SIM_ERR_PARSE, "expected 'rtlnet 1'");
+            header = true;
+            continue;
+        }
+        const char* k = tok[0];
+        int kl = tl[0];
+        if (tok_eq(k, kl, "n")) {
+            Node nd;
+            int32_t w;
+            if (nt < 3 || !tok_i32(tok[2], tl[2], w)) return fail(SIM_ERR_PARSE, "bad node");
+            int op = -1;
+            for (int i = 0; i < OP_COUNT; i++)
+                if (tok_eq(tok[1], tl[1], kOpNames[i])) op = i;
+            if (op < 0) return fail(SIM_ERR_PARSE, "unknown op");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "node width out of range");
+            nd.op = uint8_t(op);
+            nd.w = uint8_t(w);
+            int want = op == OP_MUX ? 3 : (op == OP_INPUT || op == OP_REG || op == OP_CONST) ? 1 : 2;
+            if (nt != 3 + want) return fail(SIM_ERR_PARSE, "wrong operand count");
+            if (op == OP_CONST) {
+                if (!tok_u64(tok[3], tl[3], nd.k)) return fail(SIM_ERR_PARSE, "bad constant");
+                nd.k &= mask_w(w);
+            } else {
+                int32_t v[3] = {-1, -1, -1};
+                for (int i = 0; i < want; i++)
+                    if (!tok_i32(tok[3 + i], tl[3 + i], v[i])) return fail(SIM_ERR_PARSE, "bad operand");
+                nd.a = v[0];
+                nd.b = v[1];
+                nd.c = v[2];
+            }
+            nl.nodes.push_back(nd);
+        } else if (tok_eq(k, kl, "in")) {
+            int32_t w;
+            if (nt < 2 || !tok_i32(tok[1], tl[1], w)) return fail(SIM_ERR_PARSE, "bad in");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "input width out of range");
+            nl.in_w.push_back(uint8_t(w));
+        } else if (tok_eq(k, kl, "reg")) {
+            int32_t w;
+            uint64_t init;
+            if (nt < 3 || !tok_i32(tok[1], tl[1], w) || !tok_u64(tok[2], tl[2], init))
+                return fail(SIM_ERR_PARSE, "bad reg");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "register width out of range");
+            nl.reg_w.push_back(uint8_t(w));
+            nl.reg_init.push_back(init & mask_w(w));
+            nl.reg_next.push_back(-1);
+        } else if (tok_eq(k, kl, "mem")) {
+            int32_t lg, w;
+            if (nt < 3 || !tok_i32(tok[1], tl[1], lg) || !tok_i32(tok[2], tl[2], w))
+                return fail(SIM_ERR_PARSE, "bad mem");
+            if (lg > 24) return fail(SIM_ERR_WIDTH, "memory depth out of range");
+            if (w < 1 || w > 64) return fail(SIM_ERR_WIDTH, "memory width out of range");
+            nl.mem_lg.push_back(uint8_t(lg));
+            nl.mem_w.push_back(uint8_t(w));
+            nl.mem_init.emplace_back();
+        } else if (tok_eq(k, kl, "next")) {
+            int32_t r, x;
+            if (nt != 3 || !tok_i32(tok[1], tl[1], r) || !tok_i32(tok[2], tl[2], x))
+                return fail(SIM_ERR_PARSE, "bad next");
+            nexts.emplace_back(r, x);
+        } else if (tok_eq(k, kl, "gate") || tok_eq(k, kl, "clock")) {
+            int32_t r, x;
+            if (nt != 3 || !tok_i32(tok[1], tl[1], r) || !tok_i32(tok[2], tl[2], x))
+                return fail(SIM_ERR_PARSE, "bad gate or clock item");
+            (tok_eq(k, kl, "gate") ? gate_items : clock_items).emplace_back(r, x);
+        } else if (tok_eq(k, kl, "wport")) {
+            int32_t v[4];
+            if (nt != 5) return fail(SIM_ERR_PARSE, "bad wport");
+            for (int i = 0; i < 4; i++)
+                if (!tok_i32(tok[1 + i], tl[1 + i], v[i])) return fail(SIM_ERR_PARSE, "bad wport");
+            nl.wports.push_back({v[0], v[1], v[2], v[3]});
+        } else if (tok_eq(k, kl, "minit")) {
+            int32_t m;
+            uint64_t a, v;
+            if (nt != 4 || !tok_i32(tok[1], tl[1], m) || !tok_u64(tok[2], tl[2], a) || !tok_u64(tok[3], tl[3], v))
+                return fail(SIM_ERR_PARSE, "bad minit");
+            if (m >= int32_t(nl.mem_lg.size()) || a >= (1ULL << nl.mem_lg[m]))
+                return fail(SIM_ERR_PARSE, "minit out of range");
+            nl.mem_init[m].push_back({uint32_t(a), v & mask_w(nl.mem_w[m])});
+        } else if (tok_eq(k, kl, "end")) {
+            ended = true;
+        } else {
+            return fail(SIM_ERR_PARSE, "unknown item");
+        }
+    }
+    if (!header) { err = "missing 'rtlnet 1' header"; return SIM_ERR_PARSE; }
+    if (!ended) { err = "missing 'end'"; return SIM_ERR_PARSE; }
+
+    // ---- structural checks ------------------------------------------------
+    const int32_t N = int32_t(nl.nodes.size());
+    for (auto& [r, x] : nexts) {
+        if (r < 0 || r >= int32_t(nl.reg_w.size())) { err = "next of unknown register"; return SIM_ERR_PARSE; }
+        if (nl.reg_next[r] >= 0) { err = "register has two next nodes"; return SIM_ERR_PARSE; }
+        if (x < 0 || x >= N) { err = "next node out of range"; return SIM_ERR_PARSE; }
+        nl.reg_next[r] = x;
+    }
+    for (size_t r = 0; r < nl.reg_next.size(); r++)
+        if (nl.reg_next[r] < 0) { err = "register " + std::to_string(r) + " has no next node"; return SIM_ERR_PARSE; }
+    for (auto& wp : nl.wports)
+        if (wp.mem < 0 || wp.mem >= int32_t(nl.mem_lg.size()) || wp.en >= N || wp.addr >= N || wp.data >= N) {
+            err = "write port out of range";
+            return SIM_ERR_PARSE;
+        }
+    nl.mem_ports.assign(nl.mem_lg.size(), {});
+    for (size_t p = 0; p < nl.wports.size(); p++) nl.mem_ports[nl.wports[p].mem].push_back(int32_t(p));
+
+    int rc = check_graph(nl, err);
+    if (rc) return rc;
+    if (gate_items.empty() && clock_items.empty()) return SIM_OK;
+    rc = lower_clocks(nl, gate_items, clock_items, err);
+    if (rc) return rc;
+    return check_graph(nl, err);      // levels and op count of the lowered graph
 }
 
 // ------------------------------------------------------------------------

@@ -1,0 +1,49 @@
+"""Gated and divided clocks on the CUDA path's side (CPU only): the compiler
+lowers them to a single clock, and the lowered bytecode, run by the Python
+emulator of the instruction set, reproduces the oracle (which simulates the
+clock domains phase by phase) cycle by cycle.  The loader rejects what the
+oracle rejects."""
+import pytest
+
+from paper_2403_04714_gb300 import netgen, sim
+from test_lowering_emulated import run_compare
+from test_oracle_clocks import random_clocked_circuit
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_op_compact", "lane_inst"])
+def test_clocked_design(mode):
+    text = netgen.gen_clocked().to_text()
+    run_compare(text, mode, 40, shuffle=True)
+
+
+def test_clocked_design_with_cluster_exchange():
+    text = netgen.gen_clocked().to_text()
+    run_compare(text, "lane_op_cluster", 30, target=16, cluster=(4, 2))
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+@pytest.mark.parametrize("seed", range(8))
+def test_random_clocked_circuits(mode, seed):
+    text = random_clocked_circuit(seed).to_text()
+    for target in (1, 2, 4):
+        run_compare(text, mode, 25, target=target, shuffle=True)
+
+
+def test_registers_and_signals_unchanged_by_the_lowering():
+    nl = netgen.gen_clocked()
+    info = sim.Netlist(nl.to_text(), mode="lane_op").info()
+    assert info["n_regs"] == len(nl.regs) and info["n_inputs"] == len(nl.inputs)
+
+
+def test_loader_rejections():
+    base = ["rtlnet 1", "reg 1 0", "reg 1 0", "reg 8 0", "n reg 1 0", "n reg 1 1", "n reg 8 2",
+            "next 0 0", "next 1 1", "next 2 2"]
+    bad = [base + ["clock 0 1", "clock 1 0", "end"],
+           base + ["clock 0 2", "end"],
+           base + ["clock 2 0", "clock 2 1", "end"],
+           base + ["gate 2 9", "end"],
+           ["rtlnet 1", "reg 1 0", "reg 8 0", "mem 2 8", "n reg 1 0", "n reg 8 1", "n memrd 8 0 1",
+            "next 0 0", "next 1 2", "clock 1 0", "end"]]
+    for lines in bad:
+        with pytest.raises(sim.SimError):
+            sim.Netlist("\n".join(lines), mode="lane_op")
