@@ -99,6 +99,9 @@ enum { SIM_LOWER_BYTECODE = 0, SIM_LOWER_GENERATED = 1 };
  * program stay hot in the SM).  CTA_MAJOR (generated LANE_INST only): each
  * CTA runs every instance group of its processes, so a process's code is
  * fetched by one SM.  AUTO: PROCESS_MAJOR for LANE_INST. */
+/* Partitioning strategy (sim_config.partitioner). */
+enum { SIM_PART_SLB = 0, SIM_PART_HYPERGRAPH = 1 };
+
 enum { SIM_ORDER_AUTO = 0, SIM_ORDER_GROUP_MAJOR = 1, SIM_ORDER_PROCESS_MAJOR = 2, SIM_ORDER_CTA_MAJOR = 3 };
 
 typedef struct sim_config {
@@ -124,7 +127,10 @@ typedef struct sim_config {
                                  * (not cooperative) launches: a step that runs while another persistent
                                  * launch holds SMs may not get all its CTAs at once and then ends with
                                  * SIM_ERR_TIMEOUT (never a hang). */
-    uint32_t reserved[3];
+    uint32_t partitioner;       /* SIM_PART_SLB (bottom-up merge, Sec. 5.1) or SIM_PART_HYPERGRAPH (k-way
+                                 * hypergraph partition of the fibers minimising duplicated work, the
+                                 * alternative strategy of Sec. 7) */
+    uint32_t reserved[2];
 } sim_config;
 
 typedef struct sim_netlist_info {

@@ -2,6 +2,7 @@
 #include "compiler.hpp"
 
 #include <algorithm>
+#include <array>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
@@ -800,6 +801,321 @@ struct Slb {
         return SIM_OK;
     }
 
+    // Hypergraph partitioning, the alternative strategy the paper compares
+    // with its bottom-up merge (Sec. 7, "Partitioning Strategies", after
+    // RepCut): the vertices are the fibers (after stage 1's array groups), each
+    // combinational node shared by several fibers is a hyperedge over them
+    // weighted by the node's cost (nodes with the same fibers form one
+    // hyperedge), and the processes are the parts of a k-way partition.  A
+    // hyperedge that spans lambda parts is computed lambda times, so the
+    // connectivity cut sum (lambda - 1) w(e) is exactly the duplicated work.
+    // The partition is by recursive bisection: greedy growth of one side along
+    // the heaviest connections, then Fiduccia-Mattheyses passes under a
+    // balance bound on the vertex weights (a vertex weighs its own nodes plus
+    // an equal share of each shared node).
+    struct Hg {
+        std::vector<std::vector<int32_t>> pins;     // edge -> vertices
+        std::vector<uint64_t> ew;                   // edge weight
+        std::vector<int64_t> vw;                    // vertex weight (balance)
+        std::vector<int64_t> inc_off;               // vertex -> edges (CSR)
+        std::vector<int32_t> inc;
+    };
+
+    void build_hypergraph(const std::vector<int32_t>& verts, Hg& h) const {
+        const int32_t V = int32_t(verts.size());
+        const size_t N = nl.nodes.size();
+        std::vector<int32_t> users_n(N + 1, 0);
+        for (int32_t v = 0; v < V; v++)
+            for (int32_t i : P[verts[v]].nodes) users_n[i + 1]++;
+        for (size_t i = 0; i < N; i++) users_n[i + 1] += users_n[i];
+        std::vector<int32_t> users(users_n[N]);
+        {
+            std::vector<int32_t> fill(users_n.begin(), users_n.end() - 1);
+            for (int32_t v = 0; v < V; v++)
+                for (int32_t i : P[verts[v]].nodes) users[fill[i]++] = v;   // ascending v
+        }
+        std::vector<double> share(V, 0.0);
+        h.vw.assign(V, 0);
+        std::unordered_map<uint64_t, std::vector<int32_t>> by_hash;   // pin-list hash -> edges
+        for (size_t i = 0; i < N; i++) {
+            const int32_t b = users_n[i], e = users_n[i + 1];
+            if (e == b) continue;
+            const uint64_t c = node_cost(nl, int32_t(i));
+            if (e - b == 1) { h.vw[users[b]] += int64_t(c); continue; }
+            uint64_t hs = 1469598103934665603ULL;
+            for (int32_t k = b; k < e; k++) hs = (hs ^ uint64_t(users[k])) * 1099511628211ULL;
+            int32_t found = -1;
+            for (int32_t ed : by_hash[hs])
+                if (h.pins[ed].size() == size_t(e - b) && std::equal(users.begin() + b, users.begin() + e, h.pins[ed].begin())) {
+                    found = ed;
+                    break;
+                }
+            if (found < 0) {
+                found = int32_t(h.pins.size());
+                h.pins.emplace_back(users.begin() + b, users.begin() + e);
+                h.ew.push_back(0);
+                by_hash[hs].push_back(found);
+            }
+            h.ew[found] += c;
+            for (int32_t k = b; k < e; k++) share[users[k]] += double(c) / double(e - b);
+        }
+        for (int32_t v = 0; v < V; v++) h.vw[v] += int64_t(P[verts[v]].sink) + int64_t(share[v] + 0.5) + 1;
+        h.inc_off.assign(V + 1, 0);
+        for (auto& pl : h.pins) for (int32_t v : pl) h.inc_off[v + 1]++;
+        for (int32_t v = 0; v < V; v++) h.inc_off[v + 1] += h.inc_off[v];
+        h.inc.resize(h.inc_off[V]);
+        std::vector<int64_t> fill(h.inc_off.begin(), h.inc_off.end() - 1);
+        for (size_t ed = 0; ed < h.pins.size(); ed++)
+            for (int32_t v : h.pins[ed]) h.inc[fill[v]++] = int32_t(ed);
+    }
+
+    // Split `set` into parts first_part .. first_part + k - 1 (part[v]).
+    void bisect(const Hg& h, std::vector<int32_t> set, size_t k, int32_t first_part, std::vector<int32_t>& part,
+                std::vector<int32_t>& side, std::vector<int32_t>& stamp, int32_t& epoch) const {
+        if (k <= 1) {                               // callers keep set.size() >= k
+            for (int32_t v : set) part[v] = first_part;
+            return;
+        }
+        const size_t k0 = k / 2;
+        int64_t W = 0;
+        for (int32_t v : set) W += h.vw[v];
+        const int64_t target0 = int64_t(double(W) * double(k0) / double(k));
+        const int64_t cap[2] = {int64_t(double(target0) * 1.03) + 1, int64_t(double(W - target0) * 1.03) + 1};
+        const int32_t my = ++epoch;                       // stamp[v] == my: v is in this set
+        for (int32_t v : set) { stamp[v] = my; side[v] = 1; }
+        // --- greedy growth of side 0 from the first vertex, heaviest connection first
+        std::unordered_map<int32_t, int32_t> on0;          // edge -> pins already on side 0
+        std::vector<int64_t> conn(0);
+        std::unordered_map<int32_t, int64_t> conn_of;
+        using QE = std::pair<int64_t, int32_t>;
+        std::priority_queue<QE> q;
+        int64_t w0 = 0;
+        size_t next_seed = 0;
+        while (w0 < target0) {
+            int32_t v = -1;
+            while (!q.empty()) {
+                auto [c, u] = q.top();
+                q.pop();
+                if (side[u] == 1 && conn_of[u] == c) { v = u; break; }
+            }
+            if (v < 0) {
+                while (next_seed < set.size() && side[set[next_seed]] == 0) next_seed++;
+                if (next_seed == set.size()) break;
+                v = set[next_seed];
+            }
+            side[v] = 0;
+            w0 += h.vw[v];
+            for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
+                const int32_t ed = h.inc[t];
+                if (on0[ed]++ > 0) continue;
+                for (int32_t u : h.pins[ed])
+                    if (stamp[u] == my && side[u] == 1) {
+                        int64_t& c = conn_of[u];
+                        c += int64_t(h.ew[ed]);
+                        q.push({c, u});
+                    }
+            }
+        }
+        // --- Fiduccia-Mattheyses refinement
+        std::vector<int32_t> edges;
+        for (int32_t v : set)
+            for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) edges.push_back(h.inc[t]);
+        std::sort(edges.begin(), edges.end());
+        edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+        std::unordered_map<int32_t, std::array<int32_t, 2>> cnt;
+        std::unordered_map<int32_t, int64_t> gain;
+        for (int pass = 0; pass < 4; pass++) {
+            cnt.clear();
+            for (int32_t ed : edges) {
+                std::array<int32_t, 2> c{0, 0};
+                for (int32_t u : h.pins[ed])
+                    if (stamp[u] == my) c[side[u]]++;
+                cnt[ed] = c;
+            }
+            gain.clear();
+            using GE = std::pair<int64_t, int32_t>;
+            std::priority_queue<GE> heap[2];
+            for (int32_t v : set) {
+                int64_t g = 0;
+                const int s0 = side[v];
+                for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
+                    const int32_t ed = h.inc[t];
+                    const auto& c = cnt[ed];
+                    if (c[s0] == 1) g += int64_t(h.ew[ed]);
+                    if (c[1 - s0] == 0) g -= int64_t(h.ew[ed]);
+                }
+                gain[v] = g;
+                heap[s0].push({g, v});
+            }
+            std::unordered_set<int32_t> locked;
+            std::vector<int32_t> moves;
+            int64_t cum = 0, best = 0;
+            size_t best_len = 0;
+            int64_t ws[2] = {0, 0};
+            for (int32_t v : set) ws[side[v]] += h.vw[v];
+            const size_t limit = std::max<size_t>(64, set.size() / 2);
+            while (moves.size() < limit) {
+                int32_t pick = -1;
+                int64_t pick_g = 0;
+                for (int s0 = 0; s0 < 2; s0++) {
+                    while (!heap[s0].empty()) {
+                        auto [g, u] = heap[s0].top();
+                        if (locked.count(u) || side[u] != s0 || gain[u] != g) { heap[s0].pop(); continue; }
+                        if (ws[1 - s0] + h.vw[u] > cap[1 - s0]) break;     // the best move does not fit
+                        if (pick < 0 || g > pick_g) { pick = u; pick_g = g; }
+                        break;
+                    }
+                }
+                if (pick < 0) break;
+                const int from = side[pick], to = 1 - from;
+                locked.insert(pick);
+                // gain updates of the unlocked pins of the pick's edges (FM delta rules)
+                for (int64_t t = h.inc_off[pick]; t < h.inc_off[pick + 1]; t++) {
+                    const int32_t ed = h.inc[t];
+                    auto& c = cnt[ed];
+                    const int64_t w = int64_t(h.ew[ed]);
+                    auto bump = [&](int32_t u, int64_t d) {
+                        if (stamp[u] != my || locked.count(u)) return;
+                        gain[u] += d;
+                        heap[side[u]].push({gain[u], u});
+                    };
+                    if (c[to] == 0) { for (int32_t u : h.pins[ed]) bump(u, w); }
+                    else if (c[to] == 1) {
+                        for (int32_t u : h.pins[ed])
+                            if (stamp[u] == my && side[u] == to) bump(u, -w);
+                    }
+                    c[from]--;
+                    c[to]++;
+                    if (c[from] == 0) { for (int32_t u : h.pins[ed]) bump(u, -w); }
+                    else if (c[from] == 1) {
+                        for (int32_t u : h.pins[ed])
+                            if (stamp[u] == my && side[u] == from && u != pick) bump(u, w);
+                    }
+                }
+                side[pick] = to;
+                ws[from] -= h.vw[pick];
+                ws[to] += h.vw[pick];
+                moves.push_back(pick);
+                cum += pick_g;
+                if (cum > best) { best = cum; best_len = moves.size(); }
+            }
+            for (size_t m = moves.size(); m > best_len; m--) side[moves[m - 1]] ^= 1;   // roll back
+            if (best <= 0) break;
+        }
+        std::vector<int32_t> s0, s1;
+        for (int32_t v : set) (side[v] == 0 ? s0 : s1).push_back(v);
+        // every part gets a vertex: a side with fewer vertices than parts
+        // takes the lightest vertices of the other side
+        auto top_up = [&](std::vector<int32_t>& to, std::vector<int32_t>& from, size_t need) {
+            if (to.size() >= need) return;
+            std::sort(from.begin(), from.end(), [&](int32_t a, int32_t b) { return h.vw[a] > h.vw[b]; });
+            while (to.size() < need) { to.push_back(from.back()); from.pop_back(); }
+            std::sort(from.begin(), from.end());
+            std::sort(to.begin(), to.end());
+        };
+        top_up(s0, s1, k0);
+        top_up(s1, s0, k - k0);
+        bisect(h, std::move(s0), k0, first_part, part, side, stamp, epoch);
+        bisect(h, std::move(s1), k - k0, first_part + int32_t(k0), part, side, stamp, epoch);
+    }
+
+    // Straggler relief after the hypergraph partition, whose balance bound is
+    // on estimated vertex weights: move one fiber at a time off the most
+    // expensive process to the process (among the cheapest and its
+    // communication partners) where it adds the least, while that lowers the
+    // worst cost.
+    void relieve_stragglers(size_t max_moves) {
+        using E = std::pair<uint64_t, int32_t>;
+        std::priority_queue<E> worst;
+        std::priority_queue<E, std::vector<E>, std::greater<E>> cheap;
+        for (size_t p = 0; p < P.size(); p++)
+            if (P[p].alive) { worst.push({P[p].cost, int32_t(p)}); cheap.push({P[p].cost, int32_t(p)}); }
+        std::vector<int32_t> cand, part;
+        for (size_t it = 0; it < max_moves; it++) {
+            while (!worst.empty() && (!P[worst.top().second].alive || P[worst.top().second].cost != worst.top().first))
+                worst.pop();
+            if (worst.empty()) return;
+            const int32_t p = worst.top().second;
+            if (P[p].fibers.size() < 2) return;
+            cand.clear();
+            std::vector<E> popped;
+            while (!cheap.empty() && popped.size() < 8) {
+                E e = cheap.top();
+                cheap.pop();
+                if (!P[e.second].alive || P[e.second].cost != e.first) continue;
+                popped.push_back(e);
+                if (e.second != p) cand.push_back(e.second);
+            }
+            for (auto& e : popped) cheap.push(e);
+            partners(p, part);
+            cand.insert(cand.end(), part.begin(), part.end());
+            std::sort(cand.begin(), cand.end());
+            cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+            int32_t bf = -1, bq = -1;
+            uint64_t bcost = 0;
+            for (int32_t f : P[p].fibers)
+                for (int32_t q : cand) {
+                    const uint64_t nq = P[q].cost + fib[f].cost - inter_cost(nl, fib[f].nodes, P[q].nodes);
+                    if (nq < P[p].cost && (bf < 0 || nq < bcost)) { bf = f; bq = q; bcost = nq; }
+                }
+            if (bf < 0) return;
+            // the process without the fiber
+            std::vector<int32_t> rest, u, tmp;
+            for (int32_t f : P[p].fibers)
+                if (f != bf) {
+                    rest.push_back(f);
+                    tmp.clear();
+                    std::set_union(u.begin(), u.end(), fib[f].nodes.begin(), fib[f].nodes.end(), std::back_inserter(tmp));
+                    u.swap(tmp);
+                }
+            const uint64_t sink_p = P[p].sink - sink_cost(nl, fib[bf]);
+            const uint64_t np = node_set_cost(u) + sink_p;
+            if (std::max(np, bcost) >= P[p].cost) return;
+            std::vector<int32_t> uq;
+            std::set_union(P[bq].nodes.begin(), P[bq].nodes.end(), fib[bf].nodes.begin(), fib[bf].nodes.end(),
+                           std::back_inserter(uq));
+            std::vector<int32_t> fq(P[bq].fibers);
+            fq.push_back(bf);
+            if (cfg.mem_budget_bytes && data_mem(uq, fq) > cfg.mem_budget_bytes) return;
+            P[p].nodes.swap(u);
+            P[p].fibers.swap(rest);
+            P[p].sink = sink_p;
+            P[p].cost = np;
+            P[p].mem = data_mem(P[p].nodes, P[p].fibers);
+            P[bq].nodes.swap(uq);
+            P[bq].fibers.swap(fq);
+            P[bq].sink += sink_cost(nl, fib[bf]);
+            P[bq].cost = node_set_cost(P[bq].nodes) + P[bq].sink;
+            P[bq].mem = data_mem(P[bq].nodes, P[bq].fibers);
+            proc_of_fiber[bf] = bq;
+            worst.push({P[p].cost, p});
+            worst.push({P[bq].cost, bq});
+            cheap.push({P[p].cost, p});
+            cheap.push({P[bq].cost, bq});
+        }
+    }
+
+    void hypergraph_partition(size_t target) {
+        std::vector<int32_t> verts;
+        for (size_t p = 0; p < P.size(); p++)
+            if (P[p].alive) verts.push_back(int32_t(p));
+        if (verts.size() <= target) return;
+        Hg h;
+        build_hypergraph(verts, h);
+        const int32_t V = int32_t(verts.size());
+        std::vector<int32_t> all(V), part(V, -1), side(V, 1), stamp(V, 0);
+        std::iota(all.begin(), all.end(), 0);
+        int32_t epoch = 0;
+        bisect(h, all, target, 0, part, side, stamp, epoch);
+        std::vector<int32_t> head(target, -1);
+        for (int32_t v = 0; v < V; v++) {
+            int32_t& hd = head[part[v]];
+            if (hd < 0) hd = verts[v];
+            else merge_into(hd, verts[v]);
+        }
+        relieve_stragglers(4 * target);
+    }
+
     void random_partition(size_t target, uint32_t seed) {
         std::mt19937 rng(seed);
         target = std::max<size_t>(1, std::min(target ? target : 64, P.size()));
@@ -828,6 +1144,9 @@ int partition(const Netlist& nl, const PartitionConfig& cfg, Partition& out, std
     s.init();
     if (cfg.random_seed) {
         s.random_partition(cfg.target, cfg.random_seed);
+    } else if (cfg.hypergraph) {
+        s.stage1();
+        s.hypergraph_partition(cfg.target ? cfg.target : s.P.size());
     } else {
         s.stage1();
         size_t target = cfg.target ? cfg.target : s.P.size();

@@ -59,6 +59,7 @@ struct PartitionConfig {
     uint64_t mem_budget_bytes = 0;    // per-process data-memory budget, 0 = none
     bool stage3 = true;
     uint32_t random_seed = 0;         // != 0: random balanced partition (tests)
+    bool hypergraph = false;          // RepCut-style k-way hypergraph partition instead of SLB stages 3/4
     uint32_t cand_cap = 48;           // partner candidates examined per merge
 };
 

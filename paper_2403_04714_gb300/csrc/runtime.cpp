@@ -259,6 +259,8 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
         pc.big_array_bytes = h->cfg.big_array_bytes;
         pc.stage3 = !h->cfg.disable_stage3;
         pc.random_seed = h->cfg.seed_partition;
+        if (h->cfg.partitioner > SIM_PART_HYPERGRAPH) return set_err(SIM_ERR_BADARG, "unknown partitioner");
+        pc.hypergraph = h->cfg.partitioner == SIM_PART_HYPERGRAPH;
         uint32_t target = h->cfg.target_processes;
         // defaults measured on GB300: one process per warp of 8-warp CTAs for a
         // single instance; four processes per SM with lane = instance; with

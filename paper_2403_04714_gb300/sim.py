@@ -27,6 +27,7 @@ SIM_KERNEL_PERSISTENT, SIM_KERNEL_PER_CYCLE, SIM_KERNEL_PER_CYCLE_GRAPH = 0, 1, 
 MODES = {"auto": 0, "lane_op": 1, "lane_inst": 2}
 LOWERINGS = {"bytecode": 0, "generated": 1}
 ORDERS = {"auto": 0, "group_major": 1, "process_major": 2, "cta_major": 3}
+PARTITIONERS = {"slb": 0, "hypergraph": 1}
 # generated-CUDA modules are cached here across processes
 os.environ.setdefault("RTLSIM_GENCACHE", os.path.join(os.path.dirname(PKG), "_build", "gencache"))
 KERNELS = {"persistent": 0, "per_cycle": 1, "graph": 2, "persistent_graph": 3}
@@ -46,7 +47,7 @@ class sim_config(C.Structure):
         ("digest_capacity", C.c_uint32), ("timeout_ms", C.c_uint32), ("big_array_bytes", C.c_uint64),
         ("disable_stage3", C.c_uint32), ("seed_partition", C.c_uint32), ("lowering", C.c_uint32),
         ("task_order", C.c_uint32), ("phase_samples", C.c_uint32), ("wave_groups", C.c_uint32),
-        ("cluster_size", C.c_uint32), ("reserved", C.c_uint32 * 3),
+        ("cluster_size", C.c_uint32), ("partitioner", C.c_uint32), ("reserved", C.c_uint32 * 2),
     ]
 
 
@@ -173,6 +174,8 @@ def default_config(**kw) -> sim_config:
             v = LOWERINGS[v]
         if k == "task_order" and isinstance(v, str):
             v = ORDERS[v]
+        if k == "partitioner" and isinstance(v, str):
+            v = PARTITIONERS[v]
         setattr(cfg, k, v)
     return cfg
 

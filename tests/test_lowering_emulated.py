@@ -12,8 +12,8 @@ from paper_2403_04714_gb300 import netgen, sim
 from test_oracle_bruteforce import random_tiny_circuit
 
 
-def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False, cluster=None):
-    extra = {}
+def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False, cluster=None, partitioner="slb"):
+    extra = {"partitioner": partitioner}
     if cluster:
         extra = dict(cluster_size=cluster[0], warps_per_cta=cluster[1])
     base_mode = mode.replace("_compact", "").replace("_cluster", "")
