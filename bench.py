@@ -298,6 +298,34 @@ def mesh_weak_row(stream, flush, sides=(2, 3, 4, 5, 6)):
     return out
 
 
+def partitioner_row(stream, flush, names=("tiny", "mid", "mesh_small")):
+    """The paper's comparison of partitioning strategies (Sec. 7): the
+    bottom-up merge (SLB) against a k-way hypergraph partition of the fibers,
+    one instance, the grid-barrier kernel with the default partition size."""
+    from paper_2403_04714_gb300 import netgen, sim
+    import numpy as np
+    out = {}
+    for name in names:
+        text = open(netgen.cached_netlist(name), "rb").read()
+        r = {}
+        for part in ("slb", "hypergraph"):
+            t = time.perf_counter()
+            nl = sim.Netlist(text, mode="lane_op", partitioner=part, phase_samples=500)
+            compile_s = time.perf_counter() - t
+            b = sim.Batch(nl, 1, seed=42, stream=stream)
+            ms, _ = time_steps(b, stream, 3, 1, 2000, flush)
+            b.step(500)
+            ph = np.median(b.phase_times(500)[50:], axis=0)
+            i = nl.info()
+            r[part] = {"cycles_per_s": 6000 / (sum(ms) / 1000.0), "compute_ns": float(ph[0]), "sync_ns": float(ph[1]),
+                       "processes": i["n_processes"], "process_cost_sum": i["process_cost_sum"],
+                       "process_cost_max": i["process_cost_max"], "cut_words": i["cut_words"],
+                       "steps": i["max_bundles"], "compile_s": compile_s}
+            del b, nl
+        out[name] = r
+    return out
+
+
 def cluster_row(stream, flush):
     """Cluster exchange against the plain grid-barrier kernel, one instance: a
     design that fits one 16-CTA cluster synchronises with the cluster barrier
@@ -455,7 +483,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
     ap.add_argument("--rows", default="single,batched,mesh,cluster,served",
                     help="comma list of extra rows: single, batched, mesh, cluster, served; "
-                         "opt-in sweeps: sync_sweep, mesh_weak")
+                         "opt-in sweeps: sync_sweep, mesh_weak, partitioners")
     args = ap.parse_args()
     rank, world, local, dist = (0, 1, 0, None)
     if args.impl == "reference":
@@ -566,6 +594,8 @@ def main():
             rows["sync_sweep"] = sync_sweep_row(stream)
         if "mesh_weak" in want:
             rows["mesh_weak"] = mesh_weak_row(stream, flush)
+        if "partitioners" in want:
+            rows["partitioners"] = partitioner_row(stream, flush)
 
     # ---- measured integer issue rate (the ALU roof, next to the derived one) ---
     int_peak = sim.measure_int_peak(1 << 14)
