@@ -869,11 +869,17 @@ struct Slb {
             for (int32_t v : h.pins[ed]) h.inc[fill[v]++] = int32_t(ed);
     }
 
-    // Split `set` into parts first_part .. first_part + k - 1 (part[v]).
-    void bisect(const Hg& h, std::vector<int32_t> set, size_t k, int32_t first_part, std::vector<int32_t>& part,
-                std::vector<int32_t>& side, std::vector<int32_t>& stamp, int32_t& epoch) const {
-        if (k <= 1) {                               // callers keep set.size() >= k
-            for (int32_t v : set) part[v] = first_part;
+    // Scratch arrays of the bisection, indexed by vertex or edge.
+    struct HgWork {
+        std::vector<int32_t> part, side, stamp, lock, cnt0, cnt1, on0;
+        std::vector<int64_t> gain, conn;
+        int32_t epoch = 0;
+    };
+
+    // Split `set` (size >= k) into parts first_part .. first_part + k - 1.
+    void bisect(const Hg& h, std::vector<int32_t> set, size_t k, int32_t first_part, HgWork& w) const {
+        if (k <= 1) {
+            for (int32_t v : set) w.part[v] = first_part;
             return;
         }
         const size_t k0 = k / 2;
@@ -881,12 +887,15 @@ struct Slb {
         for (int32_t v : set) W += h.vw[v];
         const int64_t target0 = int64_t(double(W) * double(k0) / double(k));
         const int64_t cap[2] = {int64_t(double(target0) * 1.03) + 1, int64_t(double(W - target0) * 1.03) + 1};
-        const int32_t my = ++epoch;                       // stamp[v] == my: v is in this set
-        for (int32_t v : set) { stamp[v] = my; side[v] = 1; }
+        const int32_t my = ++w.epoch;                     // stamp[v] == my: v is in this set
+        for (int32_t v : set) { w.stamp[v] = my; w.side[v] = 1; w.conn[v] = 0; }
+        std::vector<int32_t> edges;
+        for (int32_t v : set)
+            for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) edges.push_back(h.inc[t]);
+        std::sort(edges.begin(), edges.end());
+        edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
+        for (int32_t ed : edges) w.on0[ed] = 0;
         // --- greedy growth of side 0 from the first vertex, heaviest connection first
-        std::unordered_map<int32_t, int32_t> on0;          // edge -> pins already on side 0
-        std::vector<int64_t> conn(0);
-        std::unordered_map<int32_t, int64_t> conn_of;
         using QE = std::pair<int64_t, int32_t>;
         std::priority_queue<QE> q;
         int64_t w0 = 0;
@@ -896,63 +905,54 @@ struct Slb {
             while (!q.empty()) {
                 auto [c, u] = q.top();
                 q.pop();
-                if (side[u] == 1 && conn_of[u] == c) { v = u; break; }
+                if (w.side[u] == 1 && w.conn[u] == c) { v = u; break; }
             }
             if (v < 0) {
-                while (next_seed < set.size() && side[set[next_seed]] == 0) next_seed++;
+                while (next_seed < set.size() && w.side[set[next_seed]] == 0) next_seed++;
                 if (next_seed == set.size()) break;
                 v = set[next_seed];
             }
-            side[v] = 0;
+            w.side[v] = 0;
             w0 += h.vw[v];
             for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
                 const int32_t ed = h.inc[t];
-                if (on0[ed]++ > 0) continue;
+                if (w.on0[ed]++ > 0) continue;
                 for (int32_t u : h.pins[ed])
-                    if (stamp[u] == my && side[u] == 1) {
-                        int64_t& c = conn_of[u];
-                        c += int64_t(h.ew[ed]);
-                        q.push({c, u});
+                    if (w.stamp[u] == my && w.side[u] == 1) {
+                        w.conn[u] += int64_t(h.ew[ed]);
+                        q.push({w.conn[u], u});
                     }
             }
         }
         // --- Fiduccia-Mattheyses refinement
-        std::vector<int32_t> edges;
-        for (int32_t v : set)
-            for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) edges.push_back(h.inc[t]);
-        std::sort(edges.begin(), edges.end());
-        edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
-        std::unordered_map<int32_t, std::array<int32_t, 2>> cnt;
-        std::unordered_map<int32_t, int64_t> gain;
         for (int pass = 0; pass < 4; pass++) {
-            cnt.clear();
             for (int32_t ed : edges) {
-                std::array<int32_t, 2> c{0, 0};
+                int32_t c[2] = {0, 0};
                 for (int32_t u : h.pins[ed])
-                    if (stamp[u] == my) c[side[u]]++;
-                cnt[ed] = c;
+                    if (w.stamp[u] == my) c[w.side[u]]++;
+                w.cnt0[ed] = c[0];
+                w.cnt1[ed] = c[1];
             }
-            gain.clear();
+            auto cnt = [&](int32_t ed, int sd) -> int32_t& { return sd ? w.cnt1[ed] : w.cnt0[ed]; };
             using GE = std::pair<int64_t, int32_t>;
             std::priority_queue<GE> heap[2];
+            const int32_t lock_id = my * 8 + pass + 1;      // lock[v] == lock_id: moved in this pass
             for (int32_t v : set) {
                 int64_t g = 0;
-                const int s0 = side[v];
+                const int s0 = w.side[v];
                 for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
                     const int32_t ed = h.inc[t];
-                    const auto& c = cnt[ed];
-                    if (c[s0] == 1) g += int64_t(h.ew[ed]);
-                    if (c[1 - s0] == 0) g -= int64_t(h.ew[ed]);
+                    if (cnt(ed, s0) == 1) g += int64_t(h.ew[ed]);
+                    if (cnt(ed, 1 - s0) == 0) g -= int64_t(h.ew[ed]);
                 }
-                gain[v] = g;
+                w.gain[v] = g;
                 heap[s0].push({g, v});
             }
-            std::unordered_set<int32_t> locked;
             std::vector<int32_t> moves;
             int64_t cum = 0, best = 0;
             size_t best_len = 0;
             int64_t ws[2] = {0, 0};
-            for (int32_t v : set) ws[side[v]] += h.vw[v];
+            for (int32_t v : set) ws[w.side[v]] += h.vw[v];
             const size_t limit = std::max<size_t>(64, set.size() / 2);
             while (moves.size() < limit) {
                 int32_t pick = -1;
@@ -960,50 +960,49 @@ struct Slb {
                 for (int s0 = 0; s0 < 2; s0++) {
                     while (!heap[s0].empty()) {
                         auto [g, u] = heap[s0].top();
-                        if (locked.count(u) || side[u] != s0 || gain[u] != g) { heap[s0].pop(); continue; }
+                        if (w.lock[u] == lock_id || w.side[u] != s0 || w.gain[u] != g) { heap[s0].pop(); continue; }
                         if (ws[1 - s0] + h.vw[u] > cap[1 - s0]) break;     // the best move does not fit
                         if (pick < 0 || g > pick_g) { pick = u; pick_g = g; }
                         break;
                     }
                 }
                 if (pick < 0) break;
-                const int from = side[pick], to = 1 - from;
-                locked.insert(pick);
+                const int from = w.side[pick], to = 1 - from;
+                w.lock[pick] = lock_id;
+                auto bump = [&](int32_t u, int64_t d) {
+                    if (w.stamp[u] != my || w.lock[u] == lock_id) return;
+                    w.gain[u] += d;
+                    heap[w.side[u]].push({w.gain[u], u});
+                };
                 // gain updates of the unlocked pins of the pick's edges (FM delta rules)
                 for (int64_t t = h.inc_off[pick]; t < h.inc_off[pick + 1]; t++) {
                     const int32_t ed = h.inc[t];
-                    auto& c = cnt[ed];
-                    const int64_t w = int64_t(h.ew[ed]);
-                    auto bump = [&](int32_t u, int64_t d) {
-                        if (stamp[u] != my || locked.count(u)) return;
-                        gain[u] += d;
-                        heap[side[u]].push({gain[u], u});
-                    };
-                    if (c[to] == 0) { for (int32_t u : h.pins[ed]) bump(u, w); }
-                    else if (c[to] == 1) {
+                    const int64_t wt = int64_t(h.ew[ed]);
+                    if (cnt(ed, to) == 0) { for (int32_t u : h.pins[ed]) bump(u, wt); }
+                    else if (cnt(ed, to) == 1) {
                         for (int32_t u : h.pins[ed])
-                            if (stamp[u] == my && side[u] == to) bump(u, -w);
+                            if (w.stamp[u] == my && w.side[u] == to) bump(u, -wt);
                     }
-                    c[from]--;
-                    c[to]++;
-                    if (c[from] == 0) { for (int32_t u : h.pins[ed]) bump(u, -w); }
-                    else if (c[from] == 1) {
+                    cnt(ed, from)--;
+                    cnt(ed, to)++;
+                    if (cnt(ed, from) == 0) { for (int32_t u : h.pins[ed]) bump(u, -wt); }
+                    else if (cnt(ed, from) == 1) {
                         for (int32_t u : h.pins[ed])
-                            if (stamp[u] == my && side[u] == from && u != pick) bump(u, w);
+                            if (w.stamp[u] == my && w.side[u] == from && u != pick) bump(u, wt);
                     }
                 }
-                side[pick] = to;
+                w.side[pick] = to;
                 ws[from] -= h.vw[pick];
                 ws[to] += h.vw[pick];
                 moves.push_back(pick);
                 cum += pick_g;
                 if (cum > best) { best = cum; best_len = moves.size(); }
             }
-            for (size_t m = moves.size(); m > best_len; m--) side[moves[m - 1]] ^= 1;   // roll back
+            for (size_t m = moves.size(); m > best_len; m--) w.side[moves[m - 1]] ^= 1;   // roll back
             if (best <= 0) break;
         }
         std::vector<int32_t> s0, s1;
-        for (int32_t v : set) (side[v] == 0 ? s0 : s1).push_back(v);
+        for (int32_t v : set) (w.side[v] == 0 ? s0 : s1).push_back(v);
         // every part gets a vertex: a side with fewer vertices than parts
         // takes the lightest vertices of the other side
         auto top_up = [&](std::vector<int32_t>& to, std::vector<int32_t>& from, size_t need) {
@@ -1015,8 +1014,10 @@ struct Slb {
         };
         top_up(s0, s1, k0);
         top_up(s1, s0, k - k0);
-        bisect(h, std::move(s0), k0, first_part, part, side, stamp, epoch);
-        bisect(h, std::move(s1), k - k0, first_part + int32_t(k0), part, side, stamp, epoch);
+        set.clear();
+        set.shrink_to_fit();
+        bisect(h, std::move(s0), k0, first_part, w);
+        bisect(h, std::move(s1), k - k0, first_part + int32_t(k0), w);
     }
 
     // Straggler relief after the hypergraph partition, whose balance bound is
@@ -1031,6 +1032,7 @@ struct Slb {
         for (size_t p = 0; p < P.size(); p++)
             if (P[p].alive) { worst.push({P[p].cost, int32_t(p)}); cheap.push({P[p].cost, int32_t(p)}); }
         std::vector<int32_t> cand, part;
+        std::vector<int32_t> mult(nl.nodes.size(), 0), mult_stamp(nl.nodes.size(), 0);
         for (size_t it = 0; it < max_moves; it++) {
             while (!worst.empty() && (!P[worst.top().second].alive || P[worst.top().second].cost != worst.top().first))
                 worst.pop();
@@ -1051,13 +1053,28 @@ struct Slb {
             cand.insert(cand.end(), part.begin(), part.end());
             std::sort(cand.begin(), cand.end());
             cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-            int32_t bf = -1, bq = -1;
-            uint64_t bcost = 0;
+            std::sort(cand.begin(), cand.end(), [&](int32_t a, int32_t b) { return P[a].cost < P[b].cost; });
+            // cost of p without fiber f: minus the nodes no other fiber of p uses
             for (int32_t f : P[p].fibers)
-                for (int32_t q : cand) {
-                    const uint64_t nq = P[q].cost + fib[f].cost - inter_cost(nl, fib[f].nodes, P[q].nodes);
-                    if (nq < P[p].cost && (bf < 0 || nq < bcost)) { bf = f; bq = q; bcost = nq; }
+                for (int32_t i : fib[f].nodes) {
+                    if (mult_stamp[i] != it + 1) { mult_stamp[i] = int32_t(it + 1); mult[i] = 0; }
+                    mult[i]++;
                 }
+            int32_t bf = -1, bq = -1;
+            uint64_t bmax = P[p].cost, bp = 0;   // a move must lower the worst cost
+            for (int32_t f : P[p].fibers) {
+                uint64_t own = sink_cost(nl, fib[f]);
+                for (int32_t i : fib[f].nodes)
+                    if (mult[i] == 1) own += node_cost(nl, i);
+                const uint64_t np_f = P[p].cost - own;
+                if (np_f >= bmax) continue;
+                for (int32_t q : cand) {
+                    // lower bound: the fiber shares all its nodes with q
+                    if (P[q].cost + sink_cost(nl, fib[f]) >= bmax) break;
+                    const uint64_t nq = P[q].cost + fib[f].cost - inter_cost(nl, fib[f].nodes, P[q].nodes);
+                    if (std::max(np_f, nq) < bmax) { bf = f; bq = q; bmax = std::max(np_f, nq); bp = np_f; }
+                }
+            }
             if (bf < 0) return;
             // the process without the fiber
             std::vector<int32_t> rest, u, tmp;
@@ -1070,7 +1087,7 @@ struct Slb {
                 }
             const uint64_t sink_p = P[p].sink - sink_cost(nl, fib[bf]);
             const uint64_t np = node_set_cost(u) + sink_p;
-            if (std::max(np, bcost) >= P[p].cost) return;
+            if (np != bp) return;                        // equal by construction; stop if not
             std::vector<int32_t> uq;
             std::set_union(P[bq].nodes.begin(), P[bq].nodes.end(), fib[bf].nodes.begin(), fib[bf].nodes.end(),
                            std::back_inserter(uq));
@@ -1103,10 +1120,21 @@ struct Slb {
         Hg h;
         build_hypergraph(verts, h);
         const int32_t V = int32_t(verts.size());
-        std::vector<int32_t> all(V), part(V, -1), side(V, 1), stamp(V, 0);
+        const size_t E = h.pins.size();
+        std::vector<int32_t> all(V);
         std::iota(all.begin(), all.end(), 0);
-        int32_t epoch = 0;
-        bisect(h, all, target, 0, part, side, stamp, epoch);
+        HgWork w;
+        w.part.assign(V, -1);
+        w.side.assign(V, 1);
+        w.stamp.assign(V, 0);
+        w.lock.assign(V, 0);
+        w.gain.assign(V, 0);
+        w.conn.assign(V, 0);
+        w.cnt0.assign(E, 0);
+        w.cnt1.assign(E, 0);
+        w.on0.assign(E, 0);
+        bisect(h, all, target, 0, w);
+        const std::vector<int32_t>& part = w.part;
         std::vector<int32_t> head(target, -1);
         for (int32_t v = 0; v < V; v++) {
             int32_t& hd = head[part[v]];
