@@ -326,6 +326,44 @@ def partitioner_row(stream, flush, names=("tiny", "mid", "mesh_small")):
     return out
 
 
+def exchange_sweep_row(stream, procs=(152, 608, 2432), reads=(1, 4, 16, 64), per_proc=32, cycles=2000):
+    """Sec. 4.2 communication experiment on GB300: every process holds 32
+    registers and each register reads `reads` registers of random other
+    processes (a random balanced partition), so a process imports about
+    8 x 32 x reads bytes per cycle; the grid size m varies at fixed bytes
+    per process b.  On the paper's IPU the on-chip exchange time depended on
+    b but not on m."""
+    from paper_2403_04714_gb300 import netgen, sim
+    import numpy as np
+    out = {}
+    for d in reads:
+        line = {}
+        for P in procs:
+            if P * d > 40_000:         # the random partition of the largest cases takes tens of seconds
+                continue
+            try:
+                nl = sim.Netlist(netgen.gen_exchange(P * per_proc, d).to_text(), mode="lane_op",
+                                 target_processes=P, seed_partition=1, phase_samples=cycles)
+                b = sim.Batch(nl, 1, seed=1, stream=stream)
+            except sim.SimError as e:
+                line[str(P)] = {"unavailable": str(e)}
+                continue
+            b.step(cycles)
+            b.sync()
+            t = time.perf_counter()
+            b.step(cycles)
+            b.sync()
+            rate = cycles / (time.perf_counter() - t)
+            ph = np.median(b.phase_times(cycles)[100:], axis=0)
+            i = nl.info()
+            line[str(P)] = {"cycles_per_s": rate, "compute_ns": float(ph[0]), "sync_ns": float(ph[1]),
+                            "bytes_in_per_process": 8.0 * i["cut_words"] / P, "steps": i["max_bundles"],
+                            "launch": b.launch_info()}
+            del b, nl
+        out[f"reads_{d}"] = line
+    return out
+
+
 def cluster_row(stream, flush):
     """Cluster exchange against the plain grid-barrier kernel, one instance: a
     design that fits one 16-CTA cluster synchronises with the cluster barrier
@@ -483,7 +521,7 @@ def main():
     ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
     ap.add_argument("--rows", default="single,batched,mesh,cluster,served",
                     help="comma list of extra rows: single, batched, mesh, cluster, served; "
-                         "opt-in sweeps: sync_sweep, mesh_weak, partitioners")
+                         "opt-in sweeps: sync_sweep, exchange_sweep, mesh_weak, partitioners")
     args = ap.parse_args()
     rank, world, local, dist = (0, 1, 0, None)
     if args.impl == "reference":
@@ -594,6 +632,8 @@ def main():
             rows["sync_sweep"] = sync_sweep_row(stream)
         if "mesh_weak" in want:
             rows["mesh_weak"] = mesh_weak_row(stream, flush)
+        if "exchange_sweep" in want:
+            rows["exchange_sweep"] = exchange_sweep_row(stream)
         if "partitioners" in want:
             rows["partitioners"] = partitioner_row(stream, flush)
 

@@ -625,6 +625,28 @@ def gen_clocked(seed=1004, n_ops=2_000, n_regs=64, depth=20, n_inputs=8, gated_f
     return nl
 
 
+def gen_exchange(n_fibers: int, reads: int, seed: int = 9) -> Netlist:
+    """The communication experiment's circuit (Sec. 4.2) as a netlist: 64-bit
+    registers, each of whose next value combines its own value with `reads`
+    registers drawn at random from the whole design (an xor tree, then one
+    xorshift step).  Under a random partition nearly every read crosses
+    processes, so the values exchanged per process grow with `reads`."""
+    rng = random.Random(seed)
+    nl = Netlist()
+    regs = [nl.add_reg(64, rng.getrandbits(64) | 1) for _ in range(n_fibers)]
+    for r in regs:
+        terms = [nl.node("reg", 64, r)]
+        for _ in range(reads):
+            q = rng.randrange(n_fibers - 1)
+            terms.append(nl.node("reg", 64, q if q < r else q + 1))
+        while len(terms) > 1:
+            terms = [nl.node("xor", 64, terms[i], terms[i + 1]) if i + 1 < len(terms) else terms[i]
+                     for i in range(0, len(terms), 2)]
+        x = terms[0]
+        nl.set_next(r, nl.node("xor", 64, x, nl.node("shl", 64, x, nl.node("const", 7, 13))))
+    return nl
+
+
 def gen_mesh_small(seed=1003) -> Netlist:
     """A 2x2 mesh of 30k-op blocks: the mesh shape at served-job scale."""
     return gen_mesh(seed, mesh=2, ops_per_block=30_000, regs_per_block=2_000, depth=40, inputs_per_block=8)
