@@ -236,22 +236,23 @@ static __device__ bool cluster_barrier(uint64_t* bars, uint32_t c, uint32_t C, u
 // opcode selects one, so lanes running different operators in one schedule
 // step follow a single instruction path (no serialised divergent paths).
 __device__ __forceinline__ uint64_t alu_select(uint32_t op, uint64_t a, uint64_t b, uint64_t c, uint32_t x) {
+    // every candidate result, then a select tree on the bits of op - D_ADD
+    // (operators in enum order): four dependent selects instead of a chain
+    // of twelve
     const bool big = b >= 64;
     const uint32_t s = uint32_t(b) & 63u;
-    uint64_t r = a + b;
-    r = op == D_SUB ? a - b : r;
-    r = op == D_MUL ? a * b : r;
-    r = op == D_AND ? (a & b) : r;
-    r = op == D_OR ? (a | b) : r;
-    r = op == D_XOR ? (a ^ b) : r;
-    r = op == D_SHL ? (big ? 0ull : a << s) : r;
-    r = op == D_SHR ? (big ? 0ull : a >> s) : r;
-    r = op == D_EQ ? (uint64_t)(a == b) : r;
-    r = op == D_LT ? (uint64_t)(a < b) : r;
-    r = op == D_MUX ? (a != 0 ? b : c) : r;
-    r = op == D_SLICE ? (a >> (x & 63u)) : r;
-    r = op == D_CONCAT ? ((a << (x & 63u)) | b) : r;
-    return r;
+    const uint32_t k = op - D_ADD;
+    const bool k0 = k & 1u, k1 = k & 2u, k2 = k & 4u, k3 = k & 8u;
+    const uint64_t p0 = k0 ? a - b : a + b;                                  // ADD, SUB
+    const uint64_t p1 = k0 ? (a & b) : a * b;                                // MUL, AND
+    const uint64_t p2 = k0 ? (a ^ b) : (a | b);                              // OR, XOR
+    const uint64_t p3 = big ? 0ull : (k0 ? a >> s : a << s);                 // SHL, SHR
+    const uint64_t p4 = k0 ? (uint64_t)(a < b) : (uint64_t)(a == b);         // EQ, LT
+    const uint64_t p5 = k0 ? (a >> (x & 63u)) : (a != 0 ? b : c);            // MUX, SLICE
+    const uint64_t p6 = (a << (x & 63u)) | b;                                // CONCAT
+    const uint64_t q0 = k1 ? p1 : p0, q1 = k1 ? p3 : p2, q2 = k1 ? p5 : p4;
+    const uint64_t r0 = k2 ? q1 : q0, r1 = k2 ? p6 : q2;
+    return k3 ? r1 : r0;
 }
 
 template <bool DIGEST>
