@@ -34,9 +34,9 @@ STATE_BYTES_MID = 6126 / 8 + 7955 * 4 + 5927 * 8
 # dram__bytes_read.sum + dram__bytes_write.sum of one 10,000-cycle launch of
 # the headline kernel (ncu, 1 pass): the one-time program and table load; the
 # per-cycle exchange stays in L2 (capture: ncu --metrics dram__bytes_read.sum,
-# dram__bytes_write.sum -k regex:k_cycles_cl -s 1 -c 1 on `bench.py --no-rows
+# dram__bytes_write.sum -k regex:k_cycles -s 1 -c 1 on `bench.py --no-rows
 # --steps 2 --warmup 1`)
-HEADLINE_TRAFFIC = 4.85e6 + 0.100e6
+HEADLINE_TRAFFIC = 4.91e6 + 0.106e6
 WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
             "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
             "100k cycles; persistent kernel, autotuned geometry (grid barrier, optional cluster exchange)")
