@@ -459,6 +459,21 @@ def run_cpu_baseline(path, cycles, seed=42):
     return cycles / dt, dt
 
 
+def run_cpu_baseline_batched(path, cycles, threads, seed=42):
+    """The oracle as it stands on `threads` host threads, each simulating its
+    own instance (the oracle's C calls release the interpreter lock), for the
+    batched rows: instance-cycles per second over the bounded sample."""
+    import concurrent.futures as cf
+    import oracle
+    net = oracle.Net(path)
+    sims = [oracle.Sim(net, seed, i) for i in range(threads)]
+    t = time.perf_counter()
+    with cf.ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda s: s.run(cycles), sims))
+    dt = time.perf_counter() - t
+    return threads * cycles / dt, dt
+
+
 def host_cpu():
     """The host the oracle ran on: logical cores and CPU model."""
     model = ""
@@ -649,6 +664,15 @@ def main():
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {args.cpu_cycles} cycles of the mid netlist, 1 instance ({dt:.1f} s)",
                "host": host_cpu()}
+        for key in ("batched_4096_generated", "batched_4096_bytecode"):
+            if key in rows:
+                threads = os.cpu_count() or 1
+                cyc = max(10, args.cpu_cycles // 10)
+                vb, dtb = run_cpu_baseline_batched(path, cyc, threads)
+                rows[key]["cpu_baseline"] = {
+                    "value": vb, "unit": "instance-cycles/s", "cores": threads, "kind": "oracle",
+                    "sample": f"{threads} instances of the mid netlist, first {cyc} cycles each, one thread "
+                              f"per instance ({dtb:.1f} s)"}
 
     if rank == 0:
         out = {
