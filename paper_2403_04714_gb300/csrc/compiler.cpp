@@ -562,6 +562,7 @@ struct Slb {
     std::vector<int32_t> writer_fiber;              // register -> fiber writing it
     std::vector<std::vector<int32_t>> reader_fibers;  // register -> fibers reading it
     std::vector<std::vector<int32_t>> reads_of_fiber; // fiber -> registers read
+    std::vector<char> pinned;                         // fiber grouped by stage 1 (stays with its array)
 
     Slb(const Netlist& n, const PartitionConfig& c, std::vector<Fiber>& f) : nl(n), cfg(c), fib(f) {}
 
@@ -600,6 +601,7 @@ struct Slb {
         }
         P.resize(F);
         proc_of_fiber.resize(F);
+        pinned.assign(F, 0);
         for (size_t f = 0; f < F; f++) {
             P[f].nodes = fib[f].nodes;
             P[f].fibers = {int32_t(f)};
@@ -675,6 +677,7 @@ struct Slb {
         for (size_t m = 0; m < users.size(); m++) {
             uint64_t bytes = (uint64_t(nl.mem_w[m] + 7) / 8) << nl.mem_lg[m];
             if (bytes < cfg.big_array_bytes || users[m].size() < 2) continue;
+            for (int32_t f : users[m]) pinned[f] = 1;
             int32_t p = proc_of_fiber[users[m][0]];
             for (size_t k = 1; k < users[m].size(); k++) {
                 int32_t q = proc_of_fiber[users[m][k]];
@@ -1021,10 +1024,10 @@ struct Slb {
     }
 
     // Straggler relief after the hypergraph partition, whose balance bound is
-    // on estimated vertex weights: move one fiber at a time off the most
-    // expensive process to the process (among the cheapest and its
-    // communication partners) where it adds the least, while that lowers the
-    // worst cost.
+    // on estimated vertex weights: move one fiber at a time (never one that
+    // stage 1 grouped with a big array) off the most expensive process to the
+    // process, among the cheapest and its communication partners, that keeps
+    // the larger of the two new costs lowest, while that lowers the worst cost.
     void relieve_stragglers(size_t max_moves) {
         using E = std::pair<uint64_t, int32_t>;
         std::priority_queue<E> worst;
@@ -1063,6 +1066,7 @@ struct Slb {
             int32_t bf = -1, bq = -1;
             uint64_t bmax = P[p].cost, bp = 0;   // a move must lower the worst cost
             for (int32_t f : P[p].fibers) {
+                if (pinned[f]) continue;                 // stage 1 keeps it with its array
                 uint64_t own = sink_cost(nl, fib[f]);
                 for (int32_t i : fib[f].nodes)
                     if (mult[i] == 1) own += node_cost(nl, i);

@@ -76,3 +76,21 @@ def test_lowered_hypergraph_partition_matches_oracle(mode):
     text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
     for target in (5, 16, 40):
         run_compare(text, mode, 25, target=target, shuffle=True, partitioner="hypergraph")
+
+
+def test_stage1_array_groups_kept():
+    # the fibers reading one big array (stage 1, Sec. 5.1 footnote) stay in one
+    # process under the hypergraph partition too
+    nl = netgen.Netlist()
+    big = nl.add_mem(15, 64)                       # 256 KiB
+    small = [nl.add_mem(10, 64) for _ in range(3)]
+    owner = {}
+    for m in [big] + small:
+        for k in range(4):
+            r = nl.add_reg(64, 0)
+            nl.set_next(r, nl.node("xor", 64, nl.node("memrd", 64, m, nl.node("const", 15, k)),
+                                   nl.node("reg", 64, r)))
+            owner[r] = m
+    c = sim.Netlist(nl.to_text(), target_processes=4, partitioner="hypergraph")
+    proc, sink = c.table("fiber_proc"), c.table("fiber_sink")
+    assert len({int(proc[f]) for f in range(len(sink)) if owner[int(sink[f])] == big}) == 1
