@@ -47,3 +47,41 @@ def test_loader_rejections():
     for lines in bad:
         with pytest.raises(sim.SimError):
             sim.Netlist("\n".join(lines), mode="lane_op")
+
+
+def clocked_with_memories(seed=21):
+    """A flat design with two RAMs (write ports on the top clock), plus a
+    divide-by-2 clock for the registers whose cones read no memory."""
+    nl = netgen.gen_flat(seed, n_ops=2500, n_regs=120, depth=14, n_inputs=6, rams=((4, 64), (3, 16)))
+    div = nl.add_reg(1, 0, "clk_div2")
+    nl.set_next(div, nl.node("xor", 1, nl.node("reg", 1, div), nl.node("const", 1, 1)))
+
+    def reads_memory(root):
+        seen, st = set(), [root]
+        while st:
+            i = st.pop()
+            if i in seen:
+                continue
+            seen.add(i)
+            op, _, a = nl.nodes[i]
+            if op == "memrd":
+                return True
+            if op in ("input", "reg", "const"):
+                continue
+            st.extend([a[0]] if op == "slice" else a)
+        return False
+
+    ones = [i for i, (op, w, _) in enumerate(nl.nodes) if w == 1 and not reads_memory(i)]
+    for r in range(0, 120, 3):
+        if not reads_memory(nl.regs[r][2]):
+            nl.clocks[r] = div
+            if r % 2:
+                nl.gates[r] = ones[r % len(ones)]
+    return nl
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+def test_divided_clock_beside_memories(mode):
+    nl = clocked_with_memories()
+    assert len(nl.clocks) > 10
+    run_compare(nl.to_text(), mode, 30, target=12, shuffle=True)

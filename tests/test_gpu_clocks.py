@@ -70,3 +70,17 @@ def test_check_registers_closed_forms(clocked):
     assert b.peek_reg(0, names["clk_div4"]) == e % 2
     assert b.peek_reg(0, names["cnt_div4"]) == ((e + 1) // 2) % 65536
     assert b.peek_reg(0, names["sample_div2"]) == T % 65536          # T odd: the counter after the edge
+
+
+def test_divided_clock_beside_memories():
+    from test_clocks_lowering import clocked_with_memories
+    text = clocked_with_memories().to_text()
+    n = 2000
+    want, ref = oracle_digests(oracle.Net(text=text), 5, 0, n)
+    for cfg in (dict(mode="lane_op"), dict(mode="lane_op", cluster_size=2, warps_per_cta=2, target_processes=12)):
+        nl = sim.Netlist(text, digest_capacity=n + 1, **cfg)
+        b = sim.Batch(nl, 1, seed=5)
+        b.step(n)
+        b.sync()
+        assert np.array_equal(b.digests(0, 0, n + 1), want), cfg
+        assert np.array_equal(b.regs(0), ref.regs()), cfg
