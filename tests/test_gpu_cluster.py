@@ -36,7 +36,7 @@ def run_cluster(text, C, W, target, n, seed=42, chunks=(None,)):
     return b, plan
 
 
-@pytest.mark.parametrize("C,W,target", [(8, 1, 8), (4, 2, 8), (2, 2, 8), (16, 4, 64)])
+@pytest.mark.parametrize("C,W,target", [(8, 1, 8), (4, 2, 8), (2, 2, 8), (16, 4, 64), (6, 2, 24), (3, 1, 7)])
 def test_tiny_cluster(tiny_text, C, W, target):
     n = 3000
     b, plan = run_cluster(tiny_text, C, W, target, n, chunks=(1000, 1, 999, None))
@@ -64,6 +64,18 @@ def test_mid_clusters():
     n = 1500
     b, plan = run_cluster(text, 8, 8, 0, n, chunks=(700, None))
     assert plan[2] > 8          # several clusters: grid barrier plus mirrors
+    want, ref = oracle_digests(path, 42, 0, n, is_path=True)
+    assert first_mismatch(b.digests(0, 0, n + 1), want) is None
+    assert np.array_equal(b.regs(0), ref.regs())
+
+
+def test_mid_clusters_of_six():
+    # a cluster size that is not a power of two (6 CTAs x 4 warps)
+    path = netgen.cached_netlist("mid")
+    text = open(path).read()
+    n = 1500
+    b, plan = run_cluster(text, 6, 4, 0, n, chunks=(700, None))
+    assert plan[0] == 6 and plan[2] % 6 == 0 and plan[4] > 0
     want, ref = oracle_digests(path, 42, 0, n, is_path=True)
     assert first_mismatch(b.digests(0, 0, n + 1), want) is None
     assert np.array_equal(b.regs(0), ref.regs())
