@@ -221,45 +221,54 @@ static int lower_clocks(Netlist& nl, const std::vector<std::pair<int32_t, int32_
         return reg_read[r];
     };
     int32_t zero1 = -1;
-    // copy of the cone of `root` as domain k sees it (k = 0: the graph itself)
-    std::vector<std::vector<int32_t>> memo(size_t(max_depth) + 1);
+    // copy of the cone of `root` as domain k sees it (k = 0: the graph
+    // itself); the copies are memoised per (domain, node), in a hash map so
+    // that a long chain of divided clocks costs only the cones it visits
+    std::unordered_map<uint64_t, int32_t> memo;
     std::vector<int32_t> stack;
     auto in_domain = [&](int32_t k, int32_t root, int32_t& out) -> int {
         if (k == 0) { out = root; return SIM_OK; }
-        std::vector<int32_t>& m = memo[k];
-        if (m.empty()) m.assign(N0, -1);
+        auto key = [&](int32_t i) { return (uint64_t(uint32_t(k)) << 32) | uint32_t(i); };
+        auto get = [&](int32_t i) {
+            auto it = memo.find(key(i));
+            return it == memo.end() ? -1 : it->second;
+        };
         stack.assign(1, root);
         while (!stack.empty()) {
             const int32_t i = stack.back();
-            if (m[i] >= 0) { stack.pop_back(); continue; }
+            if (get(i) >= 0) { stack.pop_back(); continue; }
             const Node nd = nl.nodes[i];
             if (nd.op == OP_MEMRD) {
                 err = "memory read under a divided clock (node " + std::to_string(i) + ")";
                 return SIM_ERR_PARSE;
             }
             if (nd.op == OP_REG) {
-                m[i] = depth[nd.a] < k ? after[nd.a] : i;
+                memo[key(i)] = depth[nd.a] < k ? after[nd.a] : i;
                 stack.pop_back();
                 continue;
             }
-            if (nd.op == OP_INPUT || nd.op == OP_CONST) { m[i] = i; stack.pop_back(); continue; }
-            int32_t ops[3] = {nd.a, nd.op == OP_SLICE ? -1 : nd.b, nd.op == OP_MUX ? nd.c : -1};
+            if (nd.op == OP_INPUT || nd.op == OP_CONST) { memo[key(i)] = i; stack.pop_back(); continue; }
+            const int32_t ops[3] = {nd.a, nd.op == OP_SLICE ? -1 : nd.b, nd.op == OP_MUX ? nd.c : -1};
+            int32_t mapped[3] = {-1, -1, -1};
             bool ready = true;
-            for (int32_t o : ops)
-                if (o >= 0 && m[o] < 0) { stack.push_back(o); ready = false; }
+            for (int j = 0; j < 3; j++) {
+                if (ops[j] < 0) continue;
+                mapped[j] = get(ops[j]);
+                if (mapped[j] < 0) { stack.push_back(ops[j]); ready = false; }
+            }
             if (!ready) continue;
             stack.pop_back();
             bool same = true;
-            for (int32_t o : ops) same = same && (o < 0 || m[o] == o);
-            if (same) { m[i] = i; continue; }
+            for (int j = 0; j < 3; j++) same = same && (ops[j] < 0 || mapped[j] == ops[j]);
+            if (same) { memo[key(i)] = i; continue; }
             Node cp = nd;
-            cp.a = m[nd.a];
-            if (nd.op != OP_SLICE) cp.b = m[nd.b];
-            if (nd.op == OP_MUX) cp.c = m[nd.c];
+            cp.a = mapped[0];
+            if (nd.op != OP_SLICE) cp.b = mapped[1];
+            if (nd.op == OP_MUX) cp.c = mapped[2];
             nl.nodes.push_back(cp);
-            m[i] = int32_t(nl.nodes.size() - 1);
+            memo[key(i)] = int32_t(nl.nodes.size() - 1);
         }
-        out = m[root];
+        out = get(root);
         return SIM_OK;
     };
     for (int32_t k = 0; k <= max_depth; k++) {

@@ -85,3 +85,9 @@ def test_divided_clock_beside_memories(mode):
     nl = clocked_with_memories()
     assert len(nl.clocks) > 10
     run_compare(nl.to_text(), mode, 30, target=12, shuffle=True)
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+def test_deep_chain_of_divided_clocks(mode):
+    from test_oracle_clocks import ripple_counter
+    run_compare(ripple_counter(16).to_text(), mode, 70, target=4, shuffle=True)

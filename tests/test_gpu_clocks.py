@@ -84,3 +84,16 @@ def test_divided_clock_beside_memories():
         b.sync()
         assert np.array_equal(b.digests(0, 0, n + 1), want), cfg
         assert np.array_equal(b.regs(0), ref.regs()), cfg
+
+
+def test_ripple_counter_sixteen_domains_deep():
+    from test_oracle_clocks import ripple_counter
+    n_bits, n = 16, 5000
+    text = ripple_counter(n_bits).to_text()
+    want, _ = oracle_digests(oracle.Net(text=text), 1, 0, n)
+    nl = sim.Netlist(text, mode="lane_op", digest_capacity=n + 1)
+    b = sim.Batch(nl, 1, seed=1)
+    b.step(n)
+    b.sync()
+    assert np.array_equal(b.digests(0, 0, n + 1), want)
+    assert sum(int(b.peek_reg(0, i)) << i for i in range(n_bits)) == (-n) % (1 << n_bits)

@@ -170,3 +170,26 @@ def test_loader_rejections():
     mem = ["rtlnet 1", "reg 1 0", "reg 8 0", "mem 2 8", "n reg 1 0", "n reg 8 1", "n memrd 8 0 1",
            "next 0 0", "next 1 2", "clock 1 0", "end"]
     _reject("\n".join(mem), "memory read under a divided clock")
+
+
+def ripple_counter(n):
+    """n toggle registers, stage i clocked by the rising edge of stage i - 1
+    (stage 0 on the top clock): a ripple counter n clock domains deep."""
+    nl = netgen.Netlist()
+    q = [nl.add_reg(1, 0, f"q{i}") for i in range(n)]
+    for i, r in enumerate(q):
+        nl.set_next(r, nl.node("xor", 1, nl.node("reg", 1, r), nl.node("const", 1, 1)))
+        if i:
+            nl.clocks[r] = q[i - 1]
+    return nl
+
+
+def test_ripple_counter_counts_down():
+    # stage i toggles when stage i - 1 goes 0 -> 1, within the same top cycle
+    # for the whole cascade: the bits read as (-t) mod 2^n
+    n = 12
+    sim = oracle.Sim(oracle.Net(text=ripple_counter(n).to_text()), seed=1, inst=0)
+    for t in range(5000):
+        v = sum(sim.reg(i) << i for i in range(n))
+        assert v == (-t) % (1 << n), t
+        sim.run(1)
