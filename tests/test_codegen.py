@@ -1,6 +1,7 @@
 """The generated-CUDA lowering compiles and links for sm_103a on the CPU
 (NVRTC + nvJitLink need no GPU): every operator kind, memories with write
-ports and read-only memories, degenerate netlists, both lane mappings."""
+ports and read-only memories, degenerate netlists, a design with gated and
+divided clocks, both lane mappings."""
 import pytest
 
 from paper_2403_04714_gb300 import netgen, sim
@@ -20,6 +21,7 @@ def test_generated_code_compiles(mode):
     texts = [open(netgen.cached_netlist("tiny")).read()] + DEGENERATE
     texts += [random_tiny_circuit(s).to_text() for s in range(3)]
     texts.append(netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text())
+    texts.append(netgen.gen_clocked().to_text())          # gated and divided clocks, lowered at load
     for text in texts:
         nl = sim.Netlist(text, mode=mode, lowering="generated")
         r = nl.compile_generated(mode)
