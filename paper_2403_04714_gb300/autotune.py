@@ -33,7 +33,7 @@ def default_candidates(n_inst: int, sms: int = 152):
              dict(mode="lane_op", lowering="bytecode", warps_per_cta=3, target_processes=3 * sms)]
     if n_inst == 1:     # cluster exchange (one instance): several clusters, and one 16-CTA cluster
         cands += [dict(mode="lane_op", lowering="bytecode", cluster_size=c, warps_per_cta=w)
-                  for c, w in ((4, 4), (2, 4), (16, 8))]
+                  for c, w in ((4, 4), (6, 4), (2, 4), (16, 8))]
     return cands
 
 
