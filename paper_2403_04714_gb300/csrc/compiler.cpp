@@ -5,6 +5,7 @@
 #include <array>
 #include <cstdlib>
 #include <cstring>
+#include <deque>
 #include <numeric>
 #include <queue>
 #include <random>
@@ -553,6 +554,250 @@ uint64_t inter_cost(const Netlist& nl, const std::vector<int32_t>& a, const std:
 // ------------------------------------------------------------------------
 namespace {
 
+// A hypergraph over local vertex ids 0..n-1: the vertex set of one bisection,
+// or a coarsening of it (used by the hypergraph partitioning strategy).
+struct LocalHg {
+    int32_t n = 0;
+    std::vector<int64_t> vw;                  // vertex weights
+    std::vector<std::vector<int32_t>> pins;   // edge -> vertices (at least 2, ascending)
+    std::vector<int64_t> ew;                  // edge weights
+    std::vector<int64_t> inc_off;             // vertex -> edges (CSR)
+    std::vector<int32_t> inc;
+
+    void build_incidence() {
+        inc_off.assign(size_t(n) + 1, 0);
+        for (auto& pl : pins)
+            for (int32_t v : pl) inc_off[v + 1]++;
+        for (int32_t v = 0; v < n; v++) inc_off[v + 1] += inc_off[v];
+        inc.resize(inc_off[n]);
+        std::vector<int64_t> fill(inc_off.begin(), inc_off.end() - 1);
+        for (size_t e = 0; e < pins.size(); e++)
+            for (int32_t v : pins[e]) inc[fill[v]++] = int32_t(e);
+    }
+};
+
+int64_t cut_weight(const LocalHg& h, const std::vector<int8_t>& side) {
+    int64_t c = 0;
+    for (size_t e = 0; e < h.pins.size(); e++) {
+        bool on[2] = {false, false};
+        for (int32_t v : h.pins[e]) on[side[v]] = true;
+        if (on[0] && on[1]) c += h.ew[e];
+    }
+    return c;
+}
+
+// One coarsening level: every vertex pairs with the unmatched neighbour it
+// shares the most weight with (an edge of s pins adds w / (s - 1); edges of
+// more than 64 pins are ignored for the rating), if the pair stays under
+// `max_vw`.  False if the level would shrink the vertex count by under 10 %.
+bool coarsen(const LocalHg& h, int64_t max_vw, LocalHg& c, std::vector<int32_t>& map) {
+    map.assign(h.n, -1);
+    std::vector<double> score(h.n, 0.0);
+    std::vector<int32_t> touched;
+    int32_t nc = 0;
+    for (int32_t v = 0; v < h.n; v++) {
+        if (map[v] >= 0) continue;
+        touched.clear();
+        for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
+            const auto& pl = h.pins[h.inc[t]];
+            if (pl.size() > 64) continue;
+            const double r = double(h.ew[h.inc[t]]) / double(pl.size() - 1);
+            for (int32_t u : pl) {
+                if (u == v || map[u] >= 0) continue;
+                if (score[u] == 0.0) touched.push_back(u);
+                score[u] += r;
+            }
+        }
+        int32_t best = -1;
+        double bs = 0.0;
+        for (int32_t u : touched) {
+            if (h.vw[v] + h.vw[u] <= max_vw && score[u] > bs) { best = u; bs = score[u]; }
+            score[u] = 0.0;
+        }
+        map[v] = nc;
+        if (best >= 0) map[best] = nc;
+        nc++;
+    }
+    if (double(nc) > 0.9 * double(h.n)) return false;
+    c.n = nc;
+    c.vw.assign(nc, 0);
+    for (int32_t v = 0; v < h.n; v++) c.vw[map[v]] += h.vw[v];
+    c.pins.clear();
+    c.ew.clear();
+    std::vector<int32_t> pl;
+    for (size_t e = 0; e < h.pins.size(); e++) {
+        pl.clear();
+        for (int32_t v : h.pins[e]) pl.push_back(map[v]);
+        std::sort(pl.begin(), pl.end());
+        pl.erase(std::unique(pl.begin(), pl.end()), pl.end());
+        if (pl.size() < 2) continue;
+        c.pins.push_back(pl);
+        c.ew.push_back(h.ew[e]);
+    }
+    c.build_incidence();
+    return true;
+}
+
+// Greedy growth of side 0 from `seed` along the heaviest connections until
+// it weighs at least target0 (disconnected parts: the next vertex in order).
+void grow_side(const LocalHg& h, int32_t seed, int64_t target0, std::vector<int8_t>& side) {
+    side.assign(h.n, 1);
+    std::vector<int64_t> conn(h.n, 0);
+    std::vector<char> on0(h.pins.size(), 0);
+    std::priority_queue<std::pair<int64_t, int32_t>> q;
+    int64_t w0 = 0;
+    int32_t next = 0, v = seed;
+    while (w0 < target0) {
+        while (v < 0 && !q.empty()) {
+            auto [cv, u] = q.top();
+            q.pop();
+            if (side[u] == 1 && conn[u] == cv) v = u;
+        }
+        if (v < 0) {
+            while (next < h.n && side[next] == 0) next++;
+            if (next == h.n) break;
+            v = next;
+        }
+        side[v] = 0;
+        w0 += h.vw[v];
+        for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
+            const int32_t e = h.inc[t];
+            if (on0[e]) continue;
+            on0[e] = 1;
+            for (int32_t u : h.pins[e])
+                if (side[u] == 1) {
+                    conn[u] += h.ew[e];
+                    q.push({conn[u], u});
+                }
+        }
+        v = -1;
+    }
+}
+
+// Fiduccia-Mattheyses passes on a bisection: moves of the highest cut gain
+// that keep each side under its cap, each vertex once per pass, then the
+// best prefix of the pass is kept.
+void fm_refine(const LocalHg& h, std::vector<int8_t>& side, const int64_t cap[2], int passes) {
+    const size_t E = h.pins.size();
+    std::vector<int32_t> cnt[2] = {std::vector<int32_t>(E), std::vector<int32_t>(E)};
+    std::vector<int64_t> gain(h.n);
+    std::vector<int32_t> lock(h.n, 0);
+    for (int pass = 1; pass <= passes; pass++) {
+        for (size_t e = 0; e < E; e++) {
+            cnt[0][e] = cnt[1][e] = 0;
+            for (int32_t u : h.pins[e]) cnt[side[u]][e]++;
+        }
+        using GE = std::pair<int64_t, int32_t>;
+        std::priority_queue<GE> heap[2];
+        int64_t ws[2] = {0, 0};
+        for (int32_t v = 0; v < h.n; v++) {
+            const int s0 = side[v];
+            int64_t g = 0;
+            for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
+                const int32_t e = h.inc[t];
+                if (cnt[s0][e] == 1) g += h.ew[e];
+                if (cnt[1 - s0][e] == 0) g -= h.ew[e];
+            }
+            gain[v] = g;
+            heap[s0].push({g, v});
+            ws[s0] += h.vw[v];
+        }
+        std::vector<int32_t> moves;
+        int64_t cum = 0, best = 0;
+        size_t best_len = 0;
+        const size_t limit = std::max<size_t>(64, size_t(h.n) / 2);
+        while (moves.size() < limit) {
+            int32_t pick = -1;
+            int64_t pick_g = 0;
+            for (int s0 = 0; s0 < 2; s0++) {
+                while (!heap[s0].empty()) {
+                    auto [g, u] = heap[s0].top();
+                    if (lock[u] == pass || side[u] != s0 || gain[u] != g) { heap[s0].pop(); continue; }
+                    if (ws[1 - s0] + h.vw[u] > cap[1 - s0]) break;     // the best move does not fit
+                    if (pick < 0 || g > pick_g) { pick = u; pick_g = g; }
+                    break;
+                }
+            }
+            if (pick < 0) break;
+            const int from = side[pick], to = 1 - from;
+            lock[pick] = pass;
+            auto bump = [&](int32_t u, int64_t d) {
+                if (lock[u] == pass) return;
+                gain[u] += d;
+                heap[side[u]].push({gain[u], u});
+            };
+            for (int64_t t = h.inc_off[pick]; t < h.inc_off[pick + 1]; t++) {
+                const int32_t e = h.inc[t];
+                const int64_t w = h.ew[e];
+                if (cnt[to][e] == 0) { for (int32_t u : h.pins[e]) bump(u, w); }
+                else if (cnt[to][e] == 1) {
+                    for (int32_t u : h.pins[e])
+                        if (side[u] == to) bump(u, -w);
+                }
+                cnt[from][e]--;
+                cnt[to][e]++;
+                if (cnt[from][e] == 0) { for (int32_t u : h.pins[e]) bump(u, -w); }
+                else if (cnt[from][e] == 1) {
+                    for (int32_t u : h.pins[e])
+                        if (side[u] == from && u != pick) bump(u, w);
+                }
+            }
+            side[pick] = int8_t(to);
+            ws[from] -= h.vw[pick];
+            ws[to] += h.vw[pick];
+            moves.push_back(pick);
+            cum += pick_g;
+            if (cum > best) { best = cum; best_len = moves.size(); }
+        }
+        for (size_t m = moves.size(); m > best_len; m--) side[moves[m - 1]] ^= 1;   // roll back
+        if (best <= 0) break;
+    }
+}
+
+// Multilevel bisection (coarsen by heavy-connection matching, bisect the
+// coarsest level from a few seeds, then project back refining every level),
+// side 0 aiming at target0 of the weight.
+void multilevel_bisect(const LocalHg& h0, int64_t target0, std::vector<int8_t>& side) {
+    int64_t W = 0;
+    for (int64_t x : h0.vw) W += x;
+    const int64_t cap[2] = {int64_t(double(target0) * 1.03) + 1, int64_t(double(W - target0) * 1.03) + 1};
+    std::deque<LocalHg> coarse;
+    std::vector<std::vector<int32_t>> maps;
+    const LocalHg* cur = &h0;
+    const int64_t max_vw = std::max<int64_t>(1, W / 60);
+    while (cur->n > 120) {
+        LocalHg c;
+        std::vector<int32_t> m;
+        if (!coarsen(*cur, max_vw, c, m)) break;
+        coarse.push_back(std::move(c));
+        maps.push_back(std::move(m));
+        cur = &coarse.back();
+    }
+    // the coarsest level: the best of a few growth seeds, each refined
+    std::vector<int8_t> best_side, s;
+    int64_t best_cut = -1;
+    const int32_t n = cur->n;
+    for (int32_t seed : {int32_t(0), n / 3, (2 * n) / 3, n - 1}) {
+        if (seed < 0 || seed >= n) continue;
+        grow_side(*cur, seed, target0, s);
+        fm_refine(*cur, s, cap, 6);
+        const int64_t c = cut_weight(*cur, s);
+        if (best_cut < 0 || c < best_cut) { best_cut = c; best_side = s; }
+    }
+    side.swap(best_side);
+    for (size_t lv = maps.size(); lv-- > 0;) {
+        const LocalHg& fine = lv == 0 ? h0 : coarse[lv - 1];
+        std::vector<int8_t> fs(fine.n);
+        for (int32_t v = 0; v < fine.n; v++) fs[v] = side[maps[lv][v]];
+        fm_refine(fine, fs, cap, 4);
+        side.swap(fs);
+    }
+}
+
+}  // namespace
+
+namespace {
+
 struct Proc {
     std::vector<int32_t> nodes;    // sorted union of the fibers' nodes
     std::vector<int32_t> fibers;
@@ -821,10 +1066,11 @@ struct Slb {
     // hyperedge), and the processes are the parts of a k-way partition.  A
     // hyperedge that spans lambda parts is computed lambda times, so the
     // connectivity cut sum (lambda - 1) w(e) is exactly the duplicated work.
-    // The partition is by recursive bisection: greedy growth of one side along
-    // the heaviest connections, then Fiduccia-Mattheyses passes under a
-    // balance bound on the vertex weights (a vertex weighs its own nodes plus
-    // an equal share of each shared node).
+    // The partition is by recursive multilevel bisection (heavy-connection
+    // coarsening, greedy growth from a few seeds on the coarsest level,
+    // Fiduccia-Mattheyses refinement on every level) under a balance bound on
+    // the vertex weights (a vertex weighs its own nodes plus an equal share of
+    // each shared node).
     struct Hg {
         std::vector<std::vector<int32_t>> pins;     // edge -> vertices
         std::vector<uint64_t> ew;                   // edge weight
@@ -881,140 +1127,49 @@ struct Slb {
             for (int32_t v : h.pins[ed]) h.inc[fill[v]++] = int32_t(ed);
     }
 
-    // Scratch arrays of the bisection, indexed by vertex or edge.
+    // Scratch arrays of the recursive bisection, indexed by global vertex or edge.
     struct HgWork {
-        std::vector<int32_t> part, side, stamp, lock, cnt0, cnt1, on0;
-        std::vector<int64_t> gain, conn;
+        std::vector<int32_t> part, stamp, loc, estamp;
         int32_t epoch = 0;
     };
 
-    // Split `set` (size >= k) into parts first_part .. first_part + k - 1.
+    // Split `set` (ascending, size >= k) into parts first_part .. first_part + k - 1.
     void bisect(const Hg& h, std::vector<int32_t> set, size_t k, int32_t first_part, HgWork& w) const {
-        if (k <= 1) {
+        if (k <= 1) {                               // callers keep set.size() >= k
             for (int32_t v : set) w.part[v] = first_part;
             return;
         }
         const size_t k0 = k / 2;
-        int64_t W = 0;
-        for (int32_t v : set) W += h.vw[v];
-        const int64_t target0 = int64_t(double(W) * double(k0) / double(k));
-        const int64_t cap[2] = {int64_t(double(target0) * 1.03) + 1, int64_t(double(W - target0) * 1.03) + 1};
-        const int32_t my = ++w.epoch;                     // stamp[v] == my: v is in this set
-        for (int32_t v : set) { w.stamp[v] = my; w.side[v] = 1; w.conn[v] = 0; }
-        std::vector<int32_t> edges;
+        // the set's own hypergraph: its vertices, and the edges with two or more pins in it
+        const int32_t my = ++w.epoch;
+        LocalHg L;
+        L.n = int32_t(set.size());
+        L.vw.resize(set.size());
+        for (size_t i = 0; i < set.size(); i++) {
+            w.stamp[set[i]] = my;
+            w.loc[set[i]] = int32_t(i);
+            L.vw[i] = h.vw[set[i]];
+        }
+        std::vector<int32_t> pl;
         for (int32_t v : set)
-            for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) edges.push_back(h.inc[t]);
-        std::sort(edges.begin(), edges.end());
-        edges.erase(std::unique(edges.begin(), edges.end()), edges.end());
-        for (int32_t ed : edges) w.on0[ed] = 0;
-        // --- greedy growth of side 0 from the first vertex, heaviest connection first
-        using QE = std::pair<int64_t, int32_t>;
-        std::priority_queue<QE> q;
-        int64_t w0 = 0;
-        size_t next_seed = 0;
-        while (w0 < target0) {
-            int32_t v = -1;
-            while (!q.empty()) {
-                auto [c, u] = q.top();
-                q.pop();
-                if (w.side[u] == 1 && w.conn[u] == c) { v = u; break; }
-            }
-            if (v < 0) {
-                while (next_seed < set.size() && w.side[set[next_seed]] == 0) next_seed++;
-                if (next_seed == set.size()) break;
-                v = set[next_seed];
-            }
-            w.side[v] = 0;
-            w0 += h.vw[v];
             for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
                 const int32_t ed = h.inc[t];
-                if (w.on0[ed]++ > 0) continue;
+                if (w.estamp[ed] == my) continue;
+                w.estamp[ed] = my;
+                pl.clear();
                 for (int32_t u : h.pins[ed])
-                    if (w.stamp[u] == my && w.side[u] == 1) {
-                        w.conn[u] += int64_t(h.ew[ed]);
-                        q.push({w.conn[u], u});
-                    }
+                    if (w.stamp[u] == my) pl.push_back(w.loc[u]);
+                if (pl.size() < 2) continue;
+                L.pins.push_back(pl);
+                L.ew.push_back(int64_t(h.ew[ed]));
             }
-        }
-        // --- Fiduccia-Mattheyses refinement
-        for (int pass = 0; pass < 4; pass++) {
-            for (int32_t ed : edges) {
-                int32_t c[2] = {0, 0};
-                for (int32_t u : h.pins[ed])
-                    if (w.stamp[u] == my) c[w.side[u]]++;
-                w.cnt0[ed] = c[0];
-                w.cnt1[ed] = c[1];
-            }
-            auto cnt = [&](int32_t ed, int sd) -> int32_t& { return sd ? w.cnt1[ed] : w.cnt0[ed]; };
-            using GE = std::pair<int64_t, int32_t>;
-            std::priority_queue<GE> heap[2];
-            const int32_t lock_id = my * 8 + pass + 1;      // lock[v] == lock_id: moved in this pass
-            for (int32_t v : set) {
-                int64_t g = 0;
-                const int s0 = w.side[v];
-                for (int64_t t = h.inc_off[v]; t < h.inc_off[v + 1]; t++) {
-                    const int32_t ed = h.inc[t];
-                    if (cnt(ed, s0) == 1) g += int64_t(h.ew[ed]);
-                    if (cnt(ed, 1 - s0) == 0) g -= int64_t(h.ew[ed]);
-                }
-                w.gain[v] = g;
-                heap[s0].push({g, v});
-            }
-            std::vector<int32_t> moves;
-            int64_t cum = 0, best = 0;
-            size_t best_len = 0;
-            int64_t ws[2] = {0, 0};
-            for (int32_t v : set) ws[w.side[v]] += h.vw[v];
-            const size_t limit = std::max<size_t>(64, set.size() / 2);
-            while (moves.size() < limit) {
-                int32_t pick = -1;
-                int64_t pick_g = 0;
-                for (int s0 = 0; s0 < 2; s0++) {
-                    while (!heap[s0].empty()) {
-                        auto [g, u] = heap[s0].top();
-                        if (w.lock[u] == lock_id || w.side[u] != s0 || w.gain[u] != g) { heap[s0].pop(); continue; }
-                        if (ws[1 - s0] + h.vw[u] > cap[1 - s0]) break;     // the best move does not fit
-                        if (pick < 0 || g > pick_g) { pick = u; pick_g = g; }
-                        break;
-                    }
-                }
-                if (pick < 0) break;
-                const int from = w.side[pick], to = 1 - from;
-                w.lock[pick] = lock_id;
-                auto bump = [&](int32_t u, int64_t d) {
-                    if (w.stamp[u] != my || w.lock[u] == lock_id) return;
-                    w.gain[u] += d;
-                    heap[w.side[u]].push({w.gain[u], u});
-                };
-                // gain updates of the unlocked pins of the pick's edges (FM delta rules)
-                for (int64_t t = h.inc_off[pick]; t < h.inc_off[pick + 1]; t++) {
-                    const int32_t ed = h.inc[t];
-                    const int64_t wt = int64_t(h.ew[ed]);
-                    if (cnt(ed, to) == 0) { for (int32_t u : h.pins[ed]) bump(u, wt); }
-                    else if (cnt(ed, to) == 1) {
-                        for (int32_t u : h.pins[ed])
-                            if (w.stamp[u] == my && w.side[u] == to) bump(u, -wt);
-                    }
-                    cnt(ed, from)--;
-                    cnt(ed, to)++;
-                    if (cnt(ed, from) == 0) { for (int32_t u : h.pins[ed]) bump(u, -wt); }
-                    else if (cnt(ed, from) == 1) {
-                        for (int32_t u : h.pins[ed])
-                            if (w.stamp[u] == my && w.side[u] == from && u != pick) bump(u, wt);
-                    }
-                }
-                w.side[pick] = to;
-                ws[from] -= h.vw[pick];
-                ws[to] += h.vw[pick];
-                moves.push_back(pick);
-                cum += pick_g;
-                if (cum > best) { best = cum; best_len = moves.size(); }
-            }
-            for (size_t m = moves.size(); m > best_len; m--) w.side[moves[m - 1]] ^= 1;   // roll back
-            if (best <= 0) break;
-        }
+        L.build_incidence();
+        int64_t W = 0;
+        for (int64_t x : L.vw) W += x;
+        std::vector<int8_t> side;
+        multilevel_bisect(L, int64_t(double(W) * double(k0) / double(k)), side);
         std::vector<int32_t> s0, s1;
-        for (int32_t v : set) (w.side[v] == 0 ? s0 : s1).push_back(v);
+        for (size_t i = 0; i < set.size(); i++) (side[i] == 0 ? s0 : s1).push_back(set[i]);
         // every part gets a vertex: a side with fewer vertices than parts
         // takes the lightest vertices of the other side
         auto top_up = [&](std::vector<int32_t>& to, std::vector<int32_t>& from, size_t need) {
@@ -1028,6 +1183,7 @@ struct Slb {
         top_up(s1, s0, k - k0);
         set.clear();
         set.shrink_to_fit();
+        L = LocalHg();
         bisect(h, std::move(s0), k0, first_part, w);
         bisect(h, std::move(s1), k - k0, first_part + int32_t(k0), w);
     }
@@ -1138,14 +1294,9 @@ struct Slb {
         std::iota(all.begin(), all.end(), 0);
         HgWork w;
         w.part.assign(V, -1);
-        w.side.assign(V, 1);
         w.stamp.assign(V, 0);
-        w.lock.assign(V, 0);
-        w.gain.assign(V, 0);
-        w.conn.assign(V, 0);
-        w.cnt0.assign(E, 0);
-        w.cnt1.assign(E, 0);
-        w.on0.assign(E, 0);
+        w.loc.assign(V, 0);
+        w.estamp.assign(E, 0);
         bisect(h, all, target, 0, w);
         const std::vector<int32_t>& part = w.part;
         std::vector<int32_t> head(target, -1);
