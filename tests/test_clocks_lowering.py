@@ -91,3 +91,14 @@ def test_divided_clock_beside_memories(mode):
 def test_deep_chain_of_divided_clocks(mode):
     from test_oracle_clocks import ripple_counter
     run_compare(ripple_counter(16).to_text(), mode, 70, target=4, shuffle=True)
+
+
+@pytest.mark.parametrize("seed", range(30, 36))
+def test_random_designs_every_lowering_and_partitioner(seed):
+    # clocks, gates and memories together, both partitioning strategies,
+    # both lane mappings and the cluster exchange
+    text = clocked_with_memories(seed).to_text()
+    part = "hypergraph" if seed % 2 else "slb"
+    run_compare(text, "lane_op", 12, target=7, shuffle=True, partitioner=part)
+    run_compare(text, "lane_inst", 12, target=5, partitioner=part)
+    run_compare(text, "lane_op_cluster", 12, target=12, cluster=(3, 2), partitioner=part)
