@@ -1225,7 +1225,7 @@ struct Slb {
             // cost of p without fiber f: minus the nodes no other fiber of p uses
             for (int32_t f : P[p].fibers)
                 for (int32_t i : fib[f].nodes) {
-                    if (mult_stamp[i] != it + 1) { mult_stamp[i] = int32_t(it + 1); mult[i] = 0; }
+                    if (mult_stamp[i] != int32_t(it + 1)) { mult_stamp[i] = int32_t(it + 1); mult[i] = 0; }
                     mult[i]++;
                 }
             int32_t bf = -1, bq = -1;
