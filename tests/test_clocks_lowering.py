@@ -102,3 +102,9 @@ def test_random_designs_every_lowering_and_partitioner(seed):
     run_compare(text, "lane_op", 12, target=7, shuffle=True, partitioner=part)
     run_compare(text, "lane_inst", 12, target=5, partitioner=part)
     run_compare(text, "lane_op_cluster", 12, target=12, cluster=(3, 2), partitioner=part)
+
+
+@pytest.mark.parametrize("mode", ["lane_op", "lane_inst"])
+def test_gated_clock_register(mode):
+    from test_oracle_clocks import gated_divider
+    run_compare(gated_divider()[0].to_text(), mode, 60, target=2, shuffle=True)

@@ -193,3 +193,29 @@ def test_ripple_counter_counts_down():
         v = sum(sim.reg(i) << i for i in range(n))
         assert v == (-t) % (1 << n), t
         sim.run(1)
+
+
+def gated_divider():
+    """A divide-by-2 toggle whose own clock is gated by bit 0 of the 32-bit
+    LFSR, and a counter on its rising edge."""
+    nl = netgen.Netlist()
+    chk = netgen.add_check_blocks(nl)
+    d = nl.add_reg(1, 0, "div")
+    nl.set_next(d, nl.node("xor", 1, nl.node("reg", 1, d), nl.node("const", 1, 1)))
+    nl.gates[d] = nl.node("slice", 1, nl.node("reg", 32, chk["lfsr32"]), 0)
+    c = nl.add_reg(16, 0, "cnt")
+    nl.set_next(c, nl.node("add", 16, nl.node("reg", 16, c), nl.node("const", 16, 1)))
+    nl.clocks[c] = d
+    return nl, d, c
+
+
+def test_gated_divider_counts_every_second_enabled_cycle():
+    nl, d, c = gated_divider()
+    sim = oracle.Sim(oracle.Net(text=nl.to_text()), seed=1, inst=0)
+    s, enabled = 1, 0
+    for t in range(2000):
+        assert sim.reg(d) == enabled % 2
+        assert sim.reg(c) == (enabled + 1) // 2          # rising edges: enabled cycles 1, 3, 5, ...
+        enabled += s & 1
+        s = (s >> 1) ^ (LFSR32_MASK if s & 1 else 0)
+        sim.run(1)
