@@ -6,7 +6,8 @@ per CTA = 32 x warps), the task order, the lowering and, for one instance,
 the thread-block cluster size of the distributed-shared-memory exchange.  Each candidate is
 timed on a short run of the real workload with CUDA events; the best one is
 persisted in a JSON cache keyed by a hash of the netlist text, the instance
-count and the GPU name, so later runs reuse it without measuring.
+count, the GPU name and the built library, so later runs with the same
+library reuse it without measuring.
 """
 from __future__ import annotations
 
@@ -20,8 +21,23 @@ from . import sim
 CACHE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "_build", "autotune.json")
 
 
+_LIB_HASH = None
+
+
+def _lib_hash() -> str:
+    """Hash of the built simulator library: a rebuilt kernel is measured anew."""
+    global _LIB_HASH
+    if _LIB_HASH is None:
+        try:
+            with open(sim.LIB_PATH, "rb") as f:
+                _LIB_HASH = hashlib.sha256(f.read()).hexdigest()[:16]
+        except OSError:
+            _LIB_HASH = "nolib"
+    return _LIB_HASH
+
+
 def _key(text: bytes, n_inst: int, device: str) -> str:
-    return hashlib.sha256(text + f"|{n_inst}|{device}".encode()).hexdigest()[:24]
+    return hashlib.sha256(text + f"|{n_inst}|{device}|{_lib_hash()}".encode()).hexdigest()[:24]
 
 
 def default_candidates(n_inst: int, sms: int = 152):
