@@ -219,3 +219,24 @@ def test_gated_divider_counts_every_second_enabled_cycle():
         enabled += s & 1
         s = (s >> 1) ^ (LFSR32_MASK if s & 1 else 0)
         sim.run(1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_many_cycles_match_python_evaluator_with_memories(seed):
+    # larger designs (RAMs on the top clock, a divided and gated clock) over
+    # many cycles with random held inputs: oracle against the Python evaluator
+    from test_clocks_lowering import clocked_with_memories
+    nl = clocked_with_memories(500 + seed) if seed % 2 else random_clocked_circuit(10_000 + seed)
+    text = nl.to_text()
+    py = PyNet(text)
+    sim = oracle.Sim(oracle.Net(text=text), seed=3, inst=0)
+    regs, mems = py.initial_state()
+    rng = random.Random(seed)
+    for t in range(25):
+        ins = [rng.getrandbits(w) for w in py.inputs]
+        for k, v in enumerate(ins):
+            sim.hold_input(k, v)
+        sim.run(1)
+        regs, mems = py.cycle(regs, mems, ins)
+        assert [int(x) for x in sim.regs()] == regs, (seed, t)
+        assert [[sim.mem(m, a) for a in range(len(mems[m]))] for m in range(len(mems))] == mems, (seed, t)
