@@ -37,6 +37,7 @@ STATE_BYTES_MID = 6126 / 8 + 7955 * 4 + 5927 * 8
 # dram__bytes_write.sum -k regex:k_cycles -s 1 -c 1 on `bench.py --no-rows
 # --steps 2 --warmup 1`)
 HEADLINE_TRAFFIC = 4.91e6 + 0.106e6
+HBM_PEAK_GBS = 6790.0       # overwritten from MEASURED_PEAKS.json when present
 WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
             "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
             "100k cycles; persistent kernel, autotuned geometry (grid barrier, optional cluster exchange)")
@@ -449,6 +450,23 @@ def served_run(n_jobs, rate):
                      "from 1e6 to fit the bench), cap 150 GiB, 1024 slots per pool, 250-cycle steps"}
 
 
+def rows_summary(rows):
+    """The other configurations' headline numbers in a few short fields."""
+    out = {}
+    for key in ("batched_4096_generated", "batched_4096_bytecode"):
+        r = rows.get(key)
+        if r:
+            out[key] = {"instance_cycles_per_s": round(r["value"]), "cycles_timed": r["cycles_timed"],
+                        "hbm_frac_algorithmic": round(r["hbm_gbs_algorithmic"] / HBM_PEAK_GBS, 4)}
+    if "mesh_single" in rows:
+        out["mesh_2M_ops_cycles_per_s"] = round(rows["mesh_single"]["value"])
+    if "served" in rows:
+        r = rows["served"]
+        out["served"] = {"instance_cycles_per_s": round(r["value"]), "p50_s": round(r["p50_s"], 4),
+                         "p99_s": round(r["p99_s"], 4), "jobs": r["jobs"]}
+    return out
+
+
 def run_cpu_baseline(path, cycles, seed=42):
     import oracle
     net = oracle.Net(path)
@@ -532,7 +550,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-cycles", type=int, default=300)
     ap.add_argument("--cpu-cycles", type=int, default=3000, help="oracle sample for cpu_baseline")
-    ap.add_argument("--batched-cycles", type=int, default=200)
+    ap.add_argument("--batched-cycles", type=int, default=1000)
     ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
     ap.add_argument("--rows", default="single,batched,mesh,cluster,served",
                     help="comma list of extra rows: single, batched, mesh, cluster, served; "
@@ -560,6 +578,8 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
     p = peaks()
+    global HBM_PEAK_GBS
+    HBM_PEAK_GBS = float(p.get("hbm_gbs", HBM_PEAK_GBS))
 
     # ---- headline: single instance, persistent kernel, autotuned geometry ------
     from paper_2403_04714_gb300 import autotune
@@ -578,21 +598,36 @@ def main():
     peak = alu_peak_ops(p)
     geo = b.launch_info()
 
-    # ---- e2e through host buffers: held inputs in, per-instance digest out ------
+    # ---- e2e through the public call: sim_step_host, per-instance digest out ----
+    # the timed workload itself (free-running on-device stimulus, the paper's
+    # on-device test driver), host-timed around each call, which copies the
+    # step's state digest back to pinned host memory
+    out_pinned = torch.zeros(1, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
     b2 = sim.Batch(nl, 1, seed=42 + rank, stream=stream)
+    for _ in range(args.warmup):
+        b2.step_host(args.cycles, None, out_pinned)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        b2.step_host(args.cycles, None, out_pinned)
+    e2e = {"value": replica_rate(dist, world, args.steps * args.cycles, time.perf_counter() - t0), "unit": UNIT,
+           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 8,
+           "call": "sim_step_host(held_inputs=NULL): the timed workload (stimulus generated on the device), "
+                   "host-timed, state digest read back each step"}
+    del b2
+    # the same call with every input held from pinned host memory (h2d each step)
+    b3 = sim.Batch(nl, 1, seed=42 + rank, stream=stream)
     n_in = info["n_inputs"]
     held = np.arange(n_in, dtype=np.uint64).reshape(1, n_in) * np.uint64(0x9E3779B1)
     held_pinned = torch.from_numpy(held).pin_memory().numpy()
-    out_pinned = torch.zeros(1, dtype=torch.int64).pin_memory().numpy().view(np.uint64)
     for _ in range(args.warmup):
-        b2.step_host(args.cycles, held_pinned, out_pinned)
+        b3.step_host(args.cycles, held_pinned, out_pinned)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        b2.step_host(args.cycles, held_pinned, out_pinned)
-    e2e = {"value": replica_rate(dist, world, args.steps * args.cycles, time.perf_counter() - t0), "unit": UNIT,
-           "h2d_bytes_per_step": int(held.nbytes), "d2h_bytes_per_step": 8,
-           "call": "sim_step_host (all inputs held from pinned host memory, state digest read back)"}
-    del b2
+        b3.step_host(args.cycles, held_pinned, out_pinned)
+    e2e_held = {"value": replica_rate(dist, world, args.steps * args.cycles, time.perf_counter() - t0), "unit": UNIT,
+                "h2d_bytes_per_step": int(held.nbytes), "d2h_bytes_per_step": 8,
+                "call": "sim_step_host (all inputs held from pinned host memory, state digest read back)"}
+    del b3
 
     rows = {}
     want = set() if args.no_rows else set(args.rows.split(","))
@@ -683,17 +718,20 @@ def main():
                        "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "1 GPU",
                        "processes": info["n_processes"], "launch": geo,
                        "autotuned": {"config": tuned["config"], "cached": tuned["cached"],
-                                     "candidates": tuned["results"]}},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": HEADLINE_TRAFFIC,
+                                     "candidates": tuned["results"]},
+                       "rows_summary": rows_summary(rows)},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": int_peak / 1e12, "unit": "Tops/s",
+                         "frac": achieved / int_peak, "traffic": HEADLINE_TRAFFIC,
                          "kernel": "k_cycles_cl (cluster exchange)" if tuned["config"].get("cluster_size")
                                    else "k_cycles<LANE_OP> (persistent)",
-                         "measured_int_peak": int_peak / 1e12,
-                         "note": "word ops (algorithmic, unduplicated) per second; peak = 152 SMs x 64 integer-ALU "
-                                 "lanes x max SM clock (measured_int_peak: sim_measure_int_peak, independent IADD3/LOP3 "
-                                 "chains on every SM); single-instance BSP is latency-bound, see "
-                                 "rows.phases for the cycle decomposition"},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+                         "peak_source": "measured: sim_measure_int_peak (independent IADD3/LOP3 chains on every SM, "
+                                        "this run)",
+                         "derived_peak": peak / 1e12, "frac_of_derived": achieved / peak,
+                         "note": "word ops (algorithmic, unduplicated) per second of the dominant kernel; "
+                                 "derived_peak = 152 SMs x 64 integer-ALU lanes x max SM clock; single-instance BSP is "
+                                 "latency-bound, see rows.phases for the cycle decomposition"},
+            "cpu_baseline": cpu, "e2e": e2e, "e2e_held_inputs": e2e_held, "gpu_launches": launches,
+            "clocks": clk.summary(),
             "rows": rows,
             "netlist": {k: info[k] for k in ("n_ops", "n_regs", "n_fibers", "n_processes", "fiber_cost_sum",
                                              "process_cost_sum", "process_cost_max", "fiber_cost_max",

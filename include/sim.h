@@ -193,11 +193,14 @@ int sim_netlist_compile_generated(sim_netlist *nl, int32_t mode, double *seconds
  *  19 register held by each mirror entry (u32)
  *  20 {CTAs per cluster, warps per CTA, grid CTAs, mirror entries per CTA, cross-process register reads
  *      inside a cluster, reads across clusters} (u64 x 6)
+ *  21 log2 of the depth of each memory (u8)
  * Errors: BADARG. */
 int sim_netlist_table(const sim_netlist *nl, int32_t which, void *out, size_t *bytes);
 
 /* Allocate device state for n_inst instances (cudaMalloc), initialised to the
- * netlist's register init values and memory images, cycle 0.  Instance i's
+ * netlist's register init values and memory images, cycle 0.  The state is
+ * the paper's current/next split (Sec. 3.2, Fig. bsp_sim): two register
+ * buffers, the current one read and the next one written in each cycle.  Instance i's
  * stimulus key is output i+1 of the SplitMix64 stream seeded with `seed`.
  * `cuda_stream` is a cudaStream_t (NULL = legacy default stream); every
  * device operation of the batch is ordered on it.  A netlist loaded with
@@ -208,22 +211,39 @@ int sim_create_instances(sim_netlist *nl, uint32_t n_inst, uint64_t seed, void *
                          sim_batch **out);
 void sim_batch_destroy(sim_batch *b);
 
-/* Input: hold `value` (overrides the stimulus from the next cycle on, until
+/* Test-driver access between steps (Sec. 5.3, Limitations: the host does
+ * not interact with the simulation in every cycle; inputs come from the
+ * on-device stimulus unless held here).
+ * Input: hold `value` (overrides the stimulus from the next cycle on, until
  * sim_unpoke).  Register: overwrite its current value.  Takes effect before
- * the next sim_step.  Value is reduced to the signal width. */
+ * the next sim_step.  Value is reduced to the signal width.  sim_poke_mem
+ * overwrites one memory word (address below the depth, else BADARG).
+ * All three synchronise the batch's stream.  Errors: BADARG, CUDA, STATE. */
 int sim_poke(sim_batch *b, uint32_t inst, int32_t kind, uint32_t index, uint64_t value);
 int sim_unpoke(sim_batch *b, uint32_t inst, uint32_t input);
 int sim_poke_mem(sim_batch *b, uint32_t inst, uint32_t mem, uint64_t addr, uint64_t value);
 
 /* Enqueue n_cycles simulated cycles on the batch's stream (asynchronous).
- * A barrier time-out is reported by the next sim_sync. */
+ * One simulated cycle is one BSP superstep (Sec. 3.2, Fig. bsp_sim): every
+ * process reads current values, computes its registers' next values and its
+ * memories' write records (differential exchange, Sec. 5.2), then all
+ * processes meet at one barrier (the paper's two barriers become one with
+ * double-buffered state; Sec. 4.1 is the cost of that barrier).
+ * A barrier time-out is reported by the next sim_sync; after a device error
+ * the batch refuses further steps, peeks and digests with STATE until
+ * sim_restore loads a checkpoint.  Errors: BADARG, CUDA, STATE, TIMEOUT. */
 int sim_step(sim_batch *b, uint64_t n_cycles);
 int sim_sync(sim_batch *b);
 
-/* Read state after the last completed cycle (synchronises the stream). */
+/* Read state after the last completed cycle (synchronises the stream); the
+ * test driver's view of the current values (Sec. 3.2, Sec. 5.3).
+ * sim_peek_regs: all n_regs registers of one instance, in register order.
+ * sim_peek_mems: all 2^lg words of memory `mem` of one instance, in address
+ * order (out holds the memory's depth).  Errors: BADARG, CUDA, STATE. */
 int sim_peek(sim_batch *b, uint32_t inst, int32_t kind, uint32_t index, uint64_t *out);
 int sim_peek_mem(sim_batch *b, uint32_t inst, uint32_t mem, uint64_t addr, uint64_t *out);
 int sim_peek_regs(sim_batch *b, uint32_t inst, uint64_t *out /* n_regs values */);
+int sim_peek_mems(sim_batch *b, uint32_t inst, uint32_t mem, uint64_t *out /* depth values */);
 int sim_cycle(sim_batch *b, uint64_t *out);
 
 /* Digest of the current state of each instance, computed on the device:
@@ -244,9 +264,12 @@ int sim_state_digests(sim_batch *b, uint64_t *out);
  *     until the process exits.
  *   - `out` receives n_inst digests; it may be device memory or host memory
  *     (it is written with cudaMemcpyDefault).  The call synchronises.
- *   - The first call on a device looks up the array's device address for
- *     that device (with that device current); make that first call before
- *     any stream capture.
+ *   - The batch's device must be current (otherwise STATE).  The first
+ *     call on a device looks up the array's device address for that device
+ *     and keeps it; make that first call before any stream capture.  A
+ *     cudaDeviceReset invalidates that address together with every handle
+ *     of this library: do not use the library on that device afterwards in
+ *     the same process.
  *   - All calls share the one array: calls that overlap on the GPU (other
  *     threads, other streams) race and may return wrong sums. */
 int sim_state_digests_noalloc(sim_batch *b, uint64_t *out);
@@ -263,8 +286,12 @@ int sim_digests(sim_batch *b, uint32_t inst, uint64_t first_cycle, uint64_t n, u
  * copies the n_inst final state digests device->host.  Synchronises. */
 int sim_step_host(sim_batch *b, uint64_t n_cycles, const uint64_t *held_inputs, uint64_t *out_digests);
 
-/* Checkpoint: registers, memories, held inputs and the cycle counter.  The
- * blob is malloc'd by the library; release it with sim_free_blob. */
+/* Checkpoint: registers, memories, held inputs and the cycle counter, i.e.
+ * the whole current state of Sec. 3.2 (a cycle's result depends on nothing
+ * else), so a run resumed from it is the same run.  The blob is malloc'd by
+ * the library; release it with sim_free_blob.  sim_restore also clears a
+ * batch's failed state.  Errors: BADARG, OOM, CUDA, STATE (blob of another
+ * netlist or batch shape). */
 int sim_save(sim_batch *b, void **blob, size_t *len);
 int sim_restore(sim_batch *b, const void *blob, size_t len);
 void sim_free_blob(void *blob);
@@ -287,6 +314,9 @@ int sim_phase_times(sim_batch *b, uint32_t n, double *out);
 int sim_debug_skip_arrival(sim_batch *b, uint32_t timeout_ms);
 
 /* ---- serving: continuous batching of simulation jobs ---------------------
+ * The paper motivates simulation throughput by many regression runs of one
+ * design (Sec. 1 and the nightly-regression cost model of Sec. 6, Cost
+ * Comparison); here independent jobs share the device.
  * A server keeps one instance pool per netlist in device memory.  Jobs of
  * the same netlist share the pool's launches (each job's instances occupy a
  * run of slots and count cycles from their admission); pools of different

@@ -191,16 +191,24 @@ struct sim_batch {
     uint32_t cta_major = 0;
     uint64_t kernels_launched = 0;
     int32_t skip_cta = -1;
-    uint64_t timeout_ns = 2000000000ULL;
+    uint64_t timeout_ns = 2000000000ULL;   // configured barrier wait limit
+    uint64_t skip_timeout_ns = 0;          // wait limit of the one debug step that skips an arrival
+    // After a device error (a barrier time-out) a launch has left the state
+    // part-way through a cycle: the batch refuses steps, peeks and digests
+    // until sim_restore loads a checkpoint.
+    bool failed = false;
+    std::string fail_reason;
     // graph replay of per-cycle launches
     cudaGraphExec_t graph = nullptr;
     uint32_t graph_chunk = 0;
     uint32_t graph_tasks = 0;              // tasks per cycle the graph was captured for
     cudaGraphExec_t pgraph = nullptr;      // captured persistent step
     uint64_t pgraph_n = 0;
+    uint64_t pgraph_timeout = 0;
     DevState pgraph_state{};
     DevState graph_state{};               // state descriptor captured in the graph
     bool own_stream = false;
+    int device = 0;                        // device current when the batch was created
     ~sim_batch() {
         if (pool) rtl::pool_extra_free(pool);
         if (graph) cudaGraphExecDestroy(graph);
@@ -400,6 +408,7 @@ int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* b
         pick(u64);
         break;
     }
+    case 21: pick(nl->nl.mem_lg); break;
     default: return set_err(SIM_ERR_BADARG, "unknown table");
     }
     if (out) memcpy(out, src, std::min(n, *bytes));
@@ -814,9 +823,18 @@ int check_err(sim_batch* b) {
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     if (e) {
         CUDA_TRY(cudaMemsetAsync(b->err.p, 0, 4, b->stream));
-        return set_err(e, e == SIM_ERR_TIMEOUT ? "grid barrier wait timed out" : "device error");
+        const std::string what = e == SIM_ERR_TIMEOUT ? "grid barrier wait timed out" : "device error";
+        b->failed = true;
+        b->fail_reason = what + " in the step ending at cycle " + std::to_string(b->cycle);
+        return set_err(e, what);
     }
     return SIM_OK;
+}
+
+// A batch whose last launch failed holds a state part-way through a cycle.
+int refuse_failed(const sim_batch* b) {
+    if (!b->failed) return SIM_OK;
+    return set_err(SIM_ERR_STATE, "batch failed (" + b->fail_reason + "): restore a checkpoint or recreate it");
 }
 
 LaunchArgs base_args(sim_batch* b) {
@@ -876,6 +894,7 @@ int step_persistent(sim_batch* b, uint64_t n) {
     A.pending_first = 0;
     A.grid_sync = 1;
     A.skip_cta = b->skip_cta;
+    if (b->skip_cta >= 0) A.timeout_ns = b->skip_timeout_ns;   // only the debug step waits less
     b->skip_cta = -1;
     CUDA_TRY(cudaMemsetAsync(b->bar.p, 0, 8, b->stream));
     int rc = sync_state_view(b);
@@ -898,7 +917,8 @@ int step_persistent_graph(sim_batch* b, uint64_t n) {
     int rc = sync_state_view(b);
     if (rc) return rc;
     if (b->skip_cta >= 0) return step_persistent(b, n);
-    if (!b->pgraph || b->pgraph_n != n || memcmp(&b->pgraph_state, &b->S, sizeof(DevState)) != 0) {
+    if (!b->pgraph || b->pgraph_n != n || b->pgraph_timeout != b->timeout_ns ||
+        memcmp(&b->pgraph_state, &b->S, sizeof(DevState)) != 0) {
         if (b->pgraph) cudaGraphExecDestroy(b->pgraph);
         b->pgraph = nullptr;
         b->pgraph_state = b->S;
@@ -920,6 +940,7 @@ int step_persistent_graph(sim_batch* b, uint64_t n) {
         cudaGraphDestroy(g);
         CUDA_TRY(e);
         b->pgraph_n = n;
+        b->pgraph_timeout = b->timeout_ns;
     }
     CUDA_TRY(launch_set_u64(b->stream, b->t0_dev.as<uint64_t>(), b->cycle));
     CUDA_TRY(cudaGraphLaunch(b->pgraph, b->stream));
@@ -1040,6 +1061,7 @@ int create_instances(sim_netlist* nl, const sim_config& cfg, uint32_t n_inst, ui
         std::unique_ptr<sim_batch> b(new sim_batch());
         b->nl = nl;
         b->cfg = cfg;
+        CUDA_TRY(cudaGetDevice(&b->device));
         b->stream = static_cast<cudaStream_t>(cuda_stream);
         if (!b->stream) {     // a private stream (graph capture needs a non-legacy stream)
             CUDA_TRY(cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking));
@@ -1104,6 +1126,7 @@ int sim_track_digests(sim_batch* b, const uint32_t* insts, uint32_t n) {
 
 int sim_step(sim_batch* b, uint64_t n_cycles) {
     if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    if (int rc = refuse_failed(b)) return rc;
     if (n_cycles == 0) return SIM_OK;
     const uint32_t cap = b->S.ring_cap;
     uint64_t left = n_cycles;
@@ -1125,6 +1148,7 @@ int sim_step(sim_batch* b, uint64_t n_cycles) {
 
 int sim_sync(sim_batch* b) {
     if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    if (int rc = refuse_failed(b)) return rc;
     CUDA_TRY(cudaStreamSynchronize(b->stream));
     return check_err(b);
 }
@@ -1246,6 +1270,21 @@ int sim_peek_mem(sim_batch* b, uint32_t inst, uint32_t mem, uint64_t addr, uint6
     rc = sim_sync(b);
     if (rc) return rc;
     if ((rc = b->d2h(out, b->S.mem + (b->nl->mem_word_off[mem] + addr) * b->I + inst, 8))) return rc;
+    return SIM_OK;
+}
+
+int sim_peek_mems(sim_batch* b, uint32_t inst, uint32_t mem, uint64_t* out) {
+    int rc = check_inst(b, inst);
+    if (rc) return rc;
+    const Netlist& nl = b->nl->nl;
+    if (!out || mem >= nl.mem_lg.size()) return set_err(SIM_ERR_BADARG, "bad argument");
+    rc = sim_sync(b);
+    if (rc) return rc;
+    const size_t depth = size_t(1) << nl.mem_lg[mem];
+    // instance-minor layout: word a of instance inst is at (base + a) * I + inst
+    CUDA_TRY(cudaMemcpy2DAsync(out, 8, b->S.mem + b->nl->mem_word_off[mem] * b->I + inst, size_t(b->I) * 8, 8, depth,
+                               cudaMemcpyDeviceToHost, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
     return SIM_OK;
 }
 
@@ -1377,8 +1416,10 @@ int sim_save(sim_batch* b, void** blob, size_t* len) {
 
 int sim_restore(sim_batch* b, const void* blob, size_t len) {
     if (!b || !blob) return set_err(SIM_ERR_BADARG, "null argument");
-    int rc = sim_sync(b);
-    if (rc) return rc;
+    // a failed batch may be restored: wait for its stream and drop the error
+    CUDA_TRY(cudaStreamSynchronize(b->stream));
+    int rc = check_err(b);
+    if (rc && !b->failed) return rc;     // a runtime failure, not the launch's error word
     BlobHeader h;
     if (len < sizeof h) return set_err(SIM_ERR_BADARG, "checkpoint too short");
     memcpy(&h, blob, sizeof h);
@@ -1410,6 +1451,8 @@ int sim_restore(sim_batch* b, const void* blob, size_t len) {
     for (int k = 0; k < 2; k++)
         if (b->rec[k].n) CUDA_TRY(cudaMemsetAsync(b->rec[k].p, 0, b->rec[k].n, b->stream));
     b->cycle = h.cycle;
+    b->failed = false;
+    b->fail_reason.clear();
     return SIM_OK;
 }
 
@@ -1451,7 +1494,7 @@ int sim_debug_skip_arrival(sim_batch* b, uint32_t timeout_ms) {
     if (!b) return set_err(SIM_ERR_BADARG, "null batch");
     if (b->grid < 2) return set_err(SIM_ERR_STATE, "needs at least two CTAs");
     b->skip_cta = 0;
-    b->timeout_ns = uint64_t(timeout_ms) * 1000000ULL;
+    b->skip_timeout_ns = uint64_t(timeout_ms) * 1000000ULL;
     return SIM_OK;
 }
 
@@ -1463,8 +1506,9 @@ namespace rtl {
 int set_error(int code, const std::string& msg) { return set_err(code, msg); }
 
 int batch_views(sim_batch* b, DevProg* P, DevState* S, const uint64_t** mem_word_off, uint64_t* mem_words, uint32_t* I,
-                uint32_t* n_inst, uint32_t* par, cudaStream_t* stream) {
+                uint32_t* n_inst, uint32_t* par, cudaStream_t* stream, int* device) {
     if (!b) return set_err(SIM_ERR_BADARG, "null batch");
+    *device = b->device;
     *P = b->P;
     *S = b->S;
     *mem_word_off = b->mem_word_off.as<uint64_t>();

@@ -55,6 +55,7 @@ struct Pool {
     uint64_t step_n = 0;
     cudaEvent_t done_ev = nullptr;
     double idle_since = 0;
+    bool failed = false;
 };
 
 }  // namespace
@@ -71,8 +72,9 @@ struct sim_server {
     std::thread worker;
     std::vector<std::unique_ptr<Pool>> pools;   // owned by the worker thread
     size_t bytes_in_use = 0;
-    uint64_t instance_cycles = 0;
-    uint64_t kernels = 0;
+    // written by the worker, read by sim_server_stats on other threads
+    std::atomic<uint64_t> instance_cycles{0};
+    std::atomic<uint64_t> kernels{0};
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 
@@ -80,6 +82,7 @@ struct sim_server {
     bool try_admit(Job& j);
     void finish_step(Pool& p);
     void fail_pool_jobs(Pool& p, const std::string& msg);
+    void drop_failed_pools();
 };
 
 namespace {
@@ -159,6 +162,7 @@ bool sim_server::try_admit(Job& j) {
 
 void sim_server::fail_pool_jobs(Pool& p, const std::string& msg) {
     std::lock_guard<std::mutex> g(mu);
+    p.failed = true;
     for (uint64_t id : p.active) {
         Job& j = *jobs[id];
         j.state = SIM_JOB_FAILED;
@@ -168,6 +172,26 @@ void sim_server::fail_pool_jobs(Pool& p, const std::string& msg) {
     }
     p.active.clear();
     cv.notify_all();
+}
+
+// A pool whose step failed holds state part-way through a cycle: its jobs
+// have been failed, and the pool is released instead of taking new jobs.
+void sim_server::drop_failed_pools() {
+    for (auto it = pools.begin(); it != pools.end();) {
+        Pool& p = **it;
+        if (!p.failed) {
+            ++it;
+            continue;
+        }
+        cudaStreamSynchronize(rtl::pool_stream(p.batch));
+        {
+            std::lock_guard<std::mutex> g(mu);
+            bytes_in_use -= p.bytes;
+        }
+        cudaEventDestroy(p.done_ev);
+        sim_batch_destroy(p.batch);
+        it = pools.erase(it);
+    }
 }
 
 void sim_server::finish_step(Pool& p) {
@@ -264,6 +288,7 @@ void sim_server::run() {
             }
             finish_step(p);
         }
+        drop_failed_pools();
         if (!progressed) {
             std::unique_lock<std::mutex> lk(mu);
             if (!any_inflight && queue.empty())
@@ -379,8 +404,8 @@ int sim_server_wait(sim_server* s, uint64_t job_id, uint32_t timeout_ms) {
 int sim_server_stats(sim_server* s, uint64_t* instance_cycles, uint64_t* kernels, uint64_t* bytes_in_use) {
     if (!s) return rtl::set_error(SIM_ERR_BADARG, "null server");
     std::lock_guard<std::mutex> g(s->mu);
-    if (instance_cycles) *instance_cycles = s->instance_cycles;
-    if (kernels) *kernels = s->kernels;
+    if (instance_cycles) *instance_cycles = s->instance_cycles.load();
+    if (kernels) *kernels = s->kernels.load();
     if (bytes_in_use) *bytes_in_use = s->bytes_in_use;
     return SIM_OK;
 }

@@ -82,6 +82,7 @@ EXPORTS = {
     "sim_peek": (C.c_int, [C.c_void_p, C.c_uint32, C.c_int32, C.c_uint32, C.c_void_p]),
     "sim_peek_mem": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_uint64, C.c_void_p]),
     "sim_peek_regs": (C.c_int, [C.c_void_p, C.c_uint32, C.c_void_p]),
+    "sim_peek_mems": (C.c_int, [C.c_void_p, C.c_uint32, C.c_uint32, C.c_void_p]),
     "sim_cycle": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_state_digests": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sim_track_digests": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32]),
@@ -131,7 +132,7 @@ TABLES = {"s_ins": (0, None), "s_off": (1, np.uint32), "s_len": (2, np.uint32), 
           "reg_cls": (10, np.uint8), "reg_idx": (11, np.uint32), "s_slots": (12, np.uint32),
           "b_slots": (13, np.uint32), "c_words": (14, np.uint32), "c_off": (15, np.uint32),
           "c_size": (16, np.uint32), "warp_proc": (17, np.uint32), "mir_off": (18, np.uint32),
-          "mir_reg": (19, np.uint32), "cluster_plan": (20, np.uint64)}
+          "mir_reg": (19, np.uint32), "cluster_plan": (20, np.uint64), "mem_lg": (21, np.uint8)}
 # one 16-byte instruction of the device bytecode
 DINS = np.dtype([("op", np.uint8), ("w", np.uint8), ("dst", np.uint16), ("a", np.uint16), ("b", np.uint16),
                  ("c", np.uint16), ("x", np.uint16), ("imm", np.uint32)])
@@ -307,6 +308,13 @@ class Batch:
         v = C.c_uint64()
         _check(lib().sim_peek_mem(self._h, inst, m, addr, C.byref(v)))
         return v.value
+
+    def mem_all(self, inst: int, m: int) -> np.ndarray:
+        """sim_peek_mems: every word of memory m of one instance, in address order."""
+        depth = 1 << int(self.netlist.table("mem_lg")[m])
+        out = np.zeros(depth, dtype=np.uint64)
+        _check(lib().sim_peek_mems(self._h, inst, m, out.ctypes.data))
+        return out
 
     def regs(self, inst: int) -> np.ndarray:
         out = np.zeros(max(1, self.info["n_regs"]), dtype=np.uint64)

@@ -11,6 +11,7 @@ import pytest
 
 import oracle
 from paper_2403_04714_gb300 import netgen, sim
+from test_gpu_dumps import assert_same_state
 from test_gpu_parity import first_mismatch
 
 pytestmark = pytest.mark.gpu
@@ -22,8 +23,8 @@ def oracle_at(net, b, inst, seed, k):
     for r, v in enumerate(b.regs(inst)):
         ref.set_reg(r, int(v))
     for m in range(net.n_mem):
-        for a in range(net.mem_depth(m)):
-            ref.set_mem(m, a, b.peek_mem(inst, m, a))
+        for a, v in enumerate(b.mem_all(inst, m)):
+            ref.set_mem(m, a, int(v))
     ref.set_cycle(k)
     return ref
 
@@ -48,6 +49,9 @@ def windows(path, cfg, n_inst, insts, seed, ks, w):
         for i, want in zip(insts, wants):
             got = b.digests(i, k + 1, w)
             assert first_mismatch(got, want) is None, (k, i, first_mismatch(got, want))
+        # and the full state at the end of the window, word by word
+        for i, ref in zip(insts, refs):
+            assert_same_state(b, i, ref, (k + w, i))
     return b
 
 

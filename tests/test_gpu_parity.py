@@ -254,11 +254,25 @@ def test_barrier_timeout_is_reported(tiny_text, lowering):
     # step reports SIM_ERR_TIMEOUT (no fault, no unbounded wait)
     nl = sim.Netlist(tiny_text, mode="lane_op", warps_per_cta=1, lowering=lowering)
     b = sim.Batch(nl, 1, seed=1)
+    b.step(5)
+    blob = b.save()
     b.debug_skip_arrival(20)
     b.step(10)
     with pytest.raises(sim.SimError) as e:
         b.sync()
     assert e.value.name == "SIM_ERR_TIMEOUT"
+    # the failed launch left the state part-way through a cycle: the batch
+    # refuses to go on until a checkpoint is restored
+    for call in (lambda: b.step(1), b.sync, b.state_digests, lambda: b.regs(0)):
+        with pytest.raises(sim.SimError) as e:
+            call()
+        assert e.value.name == "SIM_ERR_STATE"
+    b.restore(blob)
+    b.step(95)          # the configured (long) barrier wait applies again
+    b.sync()
+    want, ref = oracle_digests(tiny_text, 1, 0, 100)
+    assert b.state_digests()[0] == want[-1]
+    assert np.array_equal(b.regs(0), ref.regs())
 
 
 def test_mesh_single_instance():

@@ -44,7 +44,11 @@ def test_random_configurations_match_the_oracle(seed):
         try:
             run_compare(nl.to_text(), mode, rng.randrange(3, 10), target=rng.randrange(1, 12),
                         shuffle=rng.random() < 0.5, partitioner=rng.choice(["slb", "hypergraph"]), **kw)
-        except sim.SimError:
+        except sim.SimError as e:
+            # only a capacity rejection (a process that does not fit the
+            # on-chip budget) is an expected outcome of a random draw
+            if e.name != "SIM_ERR_CAPACITY":
+                raise
             continue
         done += 1
-    assert done > 40
+    assert done > 60
