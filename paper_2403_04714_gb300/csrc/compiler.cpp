@@ -1441,7 +1441,11 @@ int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words
     words[base] = nb;
     uint32_t first = 0;
     for (uint32_t b = 0; b < nb; b++) {
-        words[base + 1 + b] = first | (uint32_t(steps[b].ins.size()) << 16) | steps[b].flags;
+        uint32_t groups = 0;      // operator groups of an operator step
+        if (!(steps[b].flags & kStepGeneric))
+            for (const DIns& d : steps[b].ins) groups |= 1u << ((kOpGroups >> (2 * (d.op - D_ADD))) & 3u);
+        words[base + 1 + b] = first | (uint32_t(steps[b].ins.size()) << 16) | steps[b].flags |
+                              (groups << kStepGroupShift);
         for (const DIns& d : steps[b].ins) {
             uint32_t w4[4];
             memcpy(w4, &d, 16);
@@ -1456,9 +1460,160 @@ int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words
     return SIM_OK;
 }
 
+
+// Compact program with operator chains (sim_config.chain = 2).  Operators
+// are scheduled in dependence order; an operator whose operands are all
+// ready before the step of one of them, d, and d is the only operator of its
+// lane in that step, runs in the same step on d's lane right after it,
+// taking d's result from a register instead of from the slot after a warp
+// barrier.  Each such step (kStepChain) holds the lanes' first operators,
+// then their second operators (D_NOP where a lane has none); a second
+// operator's imm bits 0/1/2 mark operands a/b/c that come from the lane's
+// first result, whose slot field names that result's slot (so the steps
+// still read as two sequential rows).  Memory reads never chain.  Slots are
+// allocated over the compact steps (a value lives from its step to the end
+// of the step of its last use).
+template <class MakeIns, class Operands>
+int chained_program(const Netlist& nl, const std::vector<Item>& items, const std::vector<int32_t>& local, size_t n_local,
+                    MakeIns& make_ins, Operands& operands, Lowered& out, size_t p, std::string& err) {
+    std::vector<size_t> commits, leaves, opers, sinks;
+    for (size_t i = 0; i < items.size(); i++)
+        (items[i].phase == 0 ? commits : items[i].phase == 1 ? leaves : items[i].phase == 2 ? opers : sinks).push_back(i);
+    const size_t no = opers.size();
+    std::vector<int32_t> op_of_local(n_local, -1);
+    for (size_t k = 0; k < no; k++) op_of_local[local[items[opers[k]].id]] = int32_t(k);
+    std::vector<int32_t> ostep(no, 0), olane(no, 0), opos(no, 0);
+    struct LaneOps { int32_t first = -1, second = -1; };
+    std::vector<std::vector<LaneOps>> lanes;
+    std::vector<uint8_t> has_memrd, has_chain;
+    std::vector<int32_t> deps;
+    for (size_t k = 0; k < no; k++) {
+        const bool memrd = nl.nodes[items[opers[k]].id].op == OP_MEMRD;
+        deps.clear();
+        operands(items[opers[k]], [&](int32_t n) {
+            const int32_t q = op_of_local[local[n]];
+            if (q >= 0) deps.push_back(q);
+        });
+        int32_t s = 0;
+        for (int32_t q : deps) s = std::max(s, ostep[q] + 1);
+        bool placed = false;
+        if (!memrd && s > 0)
+            for (int32_t d : deps) {
+                if (ostep[d] != s - 1 || opos[d] != 0) continue;
+                if (has_memrd[s - 1] || nl.nodes[items[opers[d]].id].op == OP_MEMRD) continue;
+                LaneOps& L = lanes[s - 1][olane[d]];
+                if (L.second >= 0) continue;
+                bool ok = true;
+                for (int32_t q : deps) ok &= q == d || ostep[q] < s - 1;
+                if (!ok) continue;
+                L.second = int32_t(k);
+                ostep[k] = s - 1;
+                olane[k] = olane[d];
+                opos[k] = 1;
+                has_chain[s - 1] = 1;
+                placed = true;
+                break;
+            }
+        if (placed) continue;
+        while (size_t(s) < lanes.size() && (lanes[s].size() >= 32 || (memrd && has_chain[s]))) s++;
+        if (size_t(s) == lanes.size()) {
+            lanes.emplace_back();
+            has_memrd.push_back(0);
+            has_chain.push_back(0);
+        }
+        ostep[k] = s;
+        olane[k] = int32_t(lanes[s].size());
+        opos[k] = 0;
+        lanes[s].push_back(LaneOps{int32_t(k), -1});
+        if (memrd) has_memrd[s] = 1;
+    }
+    // steps as lists of item indices (second operators after the first ones;
+    // -1 = a lane without a second operator)
+    struct PStep { uint32_t flags; std::vector<int64_t> its; uint32_t lanes; };
+    std::vector<PStep> ps;
+    for (size_t k = 0; k < commits.size(); k += 32) {
+        PStep st{kStepGeneric, {}, 0};
+        for (size_t j = k; j < std::min(commits.size(), k + 32); j++) st.its.push_back(int64_t(commits[j]));
+        ps.push_back(std::move(st));
+    }
+    for (size_t k = 0; k < leaves.size(); k += kLeafStepMax) {
+        PStep st{kStepGeneric | kStepLeaf, {}, 0};
+        for (size_t j = k; j < std::min(leaves.size(), k + kLeafStepMax); j++) st.its.push_back(int64_t(leaves[j]));
+        ps.push_back(std::move(st));
+    }
+    for (size_t s = 0; s < lanes.size(); s++) {
+        PStep st{has_memrd[s] ? kStepGeneric : has_chain[s] ? (kStepGeneric | kStepChain) : 0u, {}, 0};
+        for (auto& L : lanes[s]) st.its.push_back(int64_t(opers[L.first]));
+        if (has_chain[s])
+            for (auto& L : lanes[s]) st.its.push_back(L.second >= 0 ? int64_t(opers[L.second]) : -1);
+        st.lanes = uint32_t(lanes[s].size());
+        ps.push_back(std::move(st));
+    }
+    for (size_t k = 0; k < sinks.size(); k += 32) {
+        PStep st{kStepGeneric, {}, 0};
+        for (size_t j = k; j < std::min(sinks.size(), k + 32); j++) st.its.push_back(int64_t(sinks[j]));
+        ps.push_back(std::move(st));
+    }
+    // value lifetimes over the compact steps
+    std::vector<int32_t> last(n_local, -1), def_step(n_local, -1);
+    for (size_t b = 0; b < ps.size(); b++)
+        for (int64_t i : ps[b].its) {
+            if (i < 0) continue;
+            const Item& it = items[size_t(i)];
+            if (it.kind == 0) def_step[local[it.id]] = int32_t(b);
+            operands(it, [&](int32_t n) { last[local[n]] = std::max(last[local[n]], int32_t(b)); });
+        }
+    std::vector<uint16_t> slot(n_local, kNoSlot);
+    SlotAlloc A;
+    std::vector<std::vector<uint16_t>> release(ps.size() + 1);
+    std::vector<CStep> steps;
+    for (size_t b = 0; b < ps.size(); b++) {
+        for (uint16_t sl : release[b]) A.put(sl);
+        for (int64_t i : ps[b].its) {
+            if (i < 0 || items[size_t(i)].kind != 0) continue;
+            const int32_t l = local[items[size_t(i)].id];
+            slot[l] = A.get();
+            release[std::max(last[l], int32_t(b)) + 1].push_back(slot[l]);
+        }
+        CStep st;
+        st.flags = ps[b].flags;
+        for (size_t j = 0; j < ps[b].its.size(); j++) {
+            const int64_t i = ps[b].its[j];
+            if (i < 0) {
+                DIns nop{};                   // D_NOP (its result goes to the spare slot)
+                nop.w = 64;
+                st.ins.push_back(nop);
+                continue;
+            }
+            DIns d = make_ins(items[size_t(i)], slot);
+            if ((ps[b].flags & kStepChain) && j >= ps[b].lanes) {
+                // operands produced by this lane's first operator come from its register
+                const int64_t f = ps[b].its[j - ps[b].lanes];
+                const int32_t first_local = local[items[size_t(f)].id];
+                const Node& n = nl.nodes[items[size_t(i)].id];
+                auto from_first = [&](int32_t node) { return node >= 0 && local[node] == first_local; };
+                const bool two = n.op != OP_SLICE;
+                if (from_first(n.a)) d.imm |= 1u;
+                if (two && from_first(n.b)) d.imm |= 2u;
+                if (n.op == OP_MUX && from_first(n.c)) d.imm |= 4u;
+            }
+            st.ins.push_back(d);
+        }
+        steps.push_back(std::move(st));
+    }
+    if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
+    out.s_slots[p] = std::max<uint32_t>(out.s_slots[p], std::max<uint32_t>(1, A.next));
+    out.c_off[p] = uint32_t(out.c_words.size());
+    int rc = append_program(steps, out.c_words, err);
+    if (rc) return rc;
+    out.c_size[p] = uint32_t(out.c_words.size()) - out.c_off[p];
+    (void)def_step;
+    return SIM_OK;
+}
+
 }  // namespace
 
-int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& err) {
+int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& err, uint32_t chain) {
     RegLayout L = reg_layout(nl);
     const size_t NP = part.procs.size();
     out = Lowered();
@@ -1645,6 +1800,12 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             }
             out.s_len[p] = nb;
             out.s_slots[p] = std::max<uint32_t>(1, A.next);
+            if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
+        }
+        if (chain >= 2) {
+            int rc = chained_program(nl, items, local, nodes.size(), make_ins, operands, out, p, err);
+            if (rc) return rc;
+        } else {
             // compact copy: the occupied lanes of each row; up to four rows of
             // leaves (which never share a slot: all their consumers come later)
             // form one wide step of up to 128 instructions
@@ -1670,7 +1831,6 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             int rc = append_program(steps, out.c_words, err);
             if (rc) return rc;
             out.c_size[p] = uint32_t(out.c_words.size()) - out.c_off[p];
-            if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
         }
         // ---- LANE_INST: sequential list in depth-first post-order from each
         // sink (a value is computed right before its first consumer, which
@@ -1747,7 +1907,7 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             out.b_slots[p] = std::max<uint32_t>(1, A.next);
             if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
         }
-        out.max_bundles = std::max(out.max_bundles, out.s_len[p]);
+        out.max_bundles = std::max(out.max_bundles, out.c_words[out.c_off[p]]);   // steps of the compact program
         out.max_s_slots = std::max(out.max_s_slots, out.s_slots[p]);
         out.max_b_slots = std::max(out.max_b_slots, out.b_slots[p]);
         for (int32_t id : nodes) local[id] = -1;
@@ -1769,7 +1929,7 @@ std::vector<CStep> read_steps(const Lowered& low, size_t p) {
     std::vector<CStep> steps(nb);
     for (uint32_t b = 0; b < nb; b++) {
         const uint32_t e = w[1 + b], first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        steps[b].flags = e & (kStepGeneric | kStepLeaf);
+        steps[b].flags = e & (kStepGeneric | kStepLeaf | kStepChain);
         steps[b].ins.assign(ins + first, ins + first + cnt);
     }
     return steps;
@@ -2012,19 +2172,22 @@ int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_
     low.max_bundles = 0;
     for (size_t p = 0; p < NP; p++) {
         low.s_off[p] = uint32_t(low.s_ins.size() / 32);
-        for (const auto& st : steps[p])
-            for (size_t k = 0; k < std::max<size_t>(1, st.ins.size()); k += 32) {
+        for (const auto& st : steps[p]) {
+            // a chain step reads as two rows: the first operators, then the second ones
+            const size_t row = (st.flags & kStepChain) ? st.ins.size() / 2 : 32;
+            for (size_t k = 0; k < std::max<size_t>(1, st.ins.size()); k += row) {
                 const size_t base = low.s_ins.size();
                 low.s_ins.resize(base + 32, DIns{});
-                const size_t n = std::min<size_t>(32, st.ins.size() - std::min(k, st.ins.size()));
+                const size_t n = std::min<size_t>(row, st.ins.size() - std::min(k, st.ins.size()));
                 std::copy(st.ins.begin() + k, st.ins.begin() + k + n, low.s_ins.begin() + base);
             }
+        }
         low.s_len[p] = uint32_t(low.s_ins.size() / 32) - low.s_off[p];
-        low.max_bundles = std::max(low.max_bundles, low.s_len[p]);
         low.c_off[p] = uint32_t(low.c_words.size());
         int rc = append_program(steps[p], low.c_words, err);
         if (rc) return rc;
         low.c_size[p] = uint32_t(low.c_words.size()) - low.c_off[p];
+        low.max_bundles = std::max(low.max_bundles, low.c_words[low.c_off[p]]);
     }
     return SIM_OK;
 }

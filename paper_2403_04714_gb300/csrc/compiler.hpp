@@ -111,7 +111,9 @@ struct Lowered {
     std::vector<int32_t> commit_proc; // per memory: process holding its write ports (-1 none)
 };
 
-int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& err);
+// chain = 2: the compact programs run dependent operator pairs in one step
+// (one lane, the first result kept in a register); otherwise one level per step.
+int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& err, uint32_t chain = 0);
 
 // Cluster exchange.  Processes are placed on a grid of thread-block
 // clusters (C CTAs of W warps, one process per warp) so that producers and

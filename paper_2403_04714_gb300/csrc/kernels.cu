@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstdlib>
 #include <mutex>
 
 #include "../../include/sim.h"
@@ -255,6 +256,29 @@ __device__ __forceinline__ uint64_t alu_select(uint32_t op, uint64_t a, uint64_t
     return k3 ? r1 : r0;
 }
 
+// The same selection with fewer instructions: one left and one right shift
+// serve all four shift-like operators (the amount is b for shl/shr and the
+// static x for slice/concat), and add/sub share one adder (b complemented,
+// carry in, for sub).
+__device__ __forceinline__ uint64_t alu_select_lean(uint32_t op, uint64_t a, uint64_t b, uint64_t c, uint32_t x) {
+    const uint32_t k = op - D_ADD;
+    const bool k0 = k & 1u, k1 = k & 2u, k2 = k & 4u, k3 = k & 8u;
+    const bool dyn = (k >> 1) == 3u;                                         // SHL, SHR
+    const uint32_t s = (dyn ? uint32_t(b) : x) & 63u;
+    const uint64_t L = a << s, R = a >> s;
+    const uint64_t neg = 0ull - uint64_t(k0);
+    const uint64_t p0 = a + (b ^ neg) + uint64_t(k0);                         // ADD, SUB
+    const uint64_t p1 = k0 ? (a & b) : a * b;                                // MUL, AND
+    const uint64_t p2 = k0 ? (a ^ b) : (a | b);                              // OR, XOR
+    const uint64_t p3 = b >= 64 ? 0ull : (k0 ? R : L);                       // SHL, SHR
+    const uint64_t p4 = k0 ? (uint64_t)(a < b) : (uint64_t)(a == b);         // EQ, LT
+    const uint64_t p5 = k0 ? R : (a != 0 ? b : c);                           // MUX, SLICE
+    const uint64_t p6 = L | b;                                               // CONCAT
+    const uint64_t q0 = k1 ? p1 : p0, q1 = k1 ? p3 : p2, q2 = k1 ? p5 : p4;
+    const uint64_t r0 = k2 ? q1 : q0, r1 = k2 ? p6 : q2;
+    return k3 ? r1 : r0;
+}
+
 template <bool DIGEST>
 __device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, const DevState& S, uint32_t inst, uint64_t t,
                                              uint64_t key, int32_t col, bool pending, uint64_t* __restrict__ sl,
@@ -355,13 +379,20 @@ __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, ui
     finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
 
+// Result of one operator instruction, reduced to its width.
+template <int VAR>
+__device__ __forceinline__ uint64_t eval_op(const Dec& d, uint64_t a, uint64_t b, uint64_t c) {
+    return (VAR == 1 ? alu_select_lean(d.op, a, b, c, d.x) : alu_select(d.op, a, b, c, d.x)) & wmask(d.w);
+}
+
 // Program resident in shared memory: `prog` holds the step count, the step
 // table (first instruction | count << 16 | flags) and, 16-byte aligned, the
 // instructions.  Operator-only steps run on all 32 lanes without a branch:
 // lanes past the step's count repeat its first instruction and write the
 // spare slot `dummy` (the last word of the warp's slot region), which no
 // instruction reads.
-template <bool DIGEST>
+// VAR 1: operator steps use the lean evaluator.
+template <bool DIGEST, int VAR>
 __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t,
                                  bool pending, uint64_t* __restrict__ sl, const uint32_t* __restrict__ prog,
                                  uint32_t lane, uint32_t dummy, const uint64_t* mir_cur = nullptr,
@@ -380,7 +411,21 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
             // operator step: all 32 lanes, no branch (idle lanes write the spare slot)
             const bool on = lane < cnt;
             const Dec d = decode(ins[on ? first + lane : first]);
-            sl[on ? d.dst : dummy] = alu_select(d.op, sl[d.a], sl[d.b], sl[d.c], d.x) & wmask(d.w);
+            sl[on ? d.dst : dummy] = eval_op<VAR>(d, sl[d.a], sl[d.b], sl[d.c]);
+        } else if (e & kStepChain) {
+            // each lane: its first operator, then a second one that may take
+            // the first result from the register (imm bits 0/1/2 for a/b/c)
+            const uint32_t n = cnt >> 1;
+            const bool on = lane < n;
+            const uint32_t i1 = on ? first + lane : first;
+            const Dec d1 = decode(ins[i1]);
+            const Dec d2 = decode(ins[i1 + n]);
+            const uint64_t r1 = eval_op<VAR>(d1, sl[d1.a], sl[d1.b], sl[d1.c]);
+            sl[on ? d1.dst : dummy] = r1;
+            const uint64_t a2 = (d2.imm & 1u) ? r1 : sl[d2.a];
+            const uint64_t b2 = (d2.imm & 2u) ? r1 : sl[d2.b];
+            const uint64_t c2 = (d2.imm & 4u) ? r1 : sl[d2.c];
+            sl[on && d2.op != D_NOP ? d2.dst : dummy] = eval_op<VAR>(d2, a2, b2, c2);
         } else if (e & kStepLeaf) {
             // up to four leaves per lane, every load in flight before the
             // first value is stored; idle lanes write the spare slot
@@ -409,7 +454,7 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
 
-template <int MODE, bool DIGEST>
+template <int MODE, bool DIGEST, int VAR>
 __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -440,7 +485,7 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
             uint32_t off = 0;
             for (uint32_t p = warp; p < P.n_proc; p += tw) {
                 for (uint32_t g = 0; g < S.I; g++)
-                    task_lane_op_res<DIGEST>(P, S, p, g, t, pending, sl, prog + off, lane, A.slot_words - 1);
+                    task_lane_op_res<DIGEST, VAR>(P, S, p, g, t, pending, sl, prog + off, lane, A.slot_words - 1);
                 off += P.c_size[p];
             }
         } else {
@@ -469,7 +514,7 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
 // Mirror buffer t&1 holds cycle t's values; at launch it is filled from the
 // global state, which producers keep writing for readers in other clusters,
 // for the host and for the next launch.
-template <bool DIGEST>
+template <bool DIGEST, int VAR>
 __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
     __shared__ __align__(8) uint64_t cbar[2];
@@ -520,7 +565,7 @@ __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, Launc
         if (rec && threadIdx.x == 0) rec[0] = globaltimer_ns();
         if (p != kNoProc) {
             const uint32_t par = uint32_t(t & 1);
-            task_lane_op_res<DIGEST>(P, S, p, 0, t, pending, sl, prog, lane, slot_words - 1,
+            task_lane_op_res<DIGEST, VAR>(P, S, p, 0, t, pending, sl, prog, lane, slot_words - 1,
                                      mirror + (uint64_t)par * A.mirror_words,
                                      smem_addr(mirror + (uint64_t)(par ^ 1) * A.mirror_words));
         }
@@ -622,12 +667,32 @@ __global__ void k_state_digest(DevProg P, DevState S, uint32_t par, const uint64
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
-template <int MODE, bool DIGEST>
-static void* kfun() { return reinterpret_cast<void*>(&k_cycles<MODE, DIGEST>); }
+template <int MODE, bool DIGEST, int VAR>
+static void* kfun() { return reinterpret_cast<void*>(&k_cycles<MODE, DIGEST, VAR>); }
+
+// interpreter variant of the LANE_OP kernels (experiments: RTLSIM_VARIANT)
+static int variant() {
+    static const int v = [] {
+        const char* e = getenv("RTLSIM_VARIANT");
+        return e ? (atoi(e) & 3) : 0;
+    }();
+    return v;
+}
+
+template <bool DIGEST>
+static void* lane_op_fn() {
+    switch (variant()) {
+    case 1: return kfun<SIM_MODE_LANE_OP, DIGEST, 1>();
+    case 2: return kfun<SIM_MODE_LANE_OP, DIGEST, 2>();
+    case 3: return kfun<SIM_MODE_LANE_OP, DIGEST, 3>();
+    default: return kfun<SIM_MODE_LANE_OP, DIGEST, 0>();
+    }
+}
 
 static void* cycles_fn(int mode, bool digest) {
-    if (mode == SIM_MODE_LANE_INST) return digest ? kfun<SIM_MODE_LANE_INST, true>() : kfun<SIM_MODE_LANE_INST, false>();
-    return digest ? kfun<SIM_MODE_LANE_OP, true>() : kfun<SIM_MODE_LANE_OP, false>();
+    if (mode == SIM_MODE_LANE_INST)
+        return digest ? kfun<SIM_MODE_LANE_INST, true, 0>() : kfun<SIM_MODE_LANE_INST, false, 0>();
+    return digest ? lane_op_fn<true>() : lane_op_fn<false>();
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by every
@@ -661,9 +726,17 @@ cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
 }
 
-static void* cycles_cl_fn(bool digest) {
-    return digest ? reinterpret_cast<void*>(&k_cycles_cl<true>) : reinterpret_cast<void*>(&k_cycles_cl<false>);
+template <bool DIGEST>
+static void* cycles_cl_var() {
+    switch (variant()) {
+    case 1: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 1>);
+    case 2: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 2>);
+    case 3: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 3>);
+    default: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 0>);
+    }
 }
+
+static void* cycles_cl_fn(bool digest) { return digest ? cycles_cl_var<true>() : cycles_cl_var<false>(); }
 
 // Shared-memory limit (monotonic, as for k_cycles) and, above the portable
 // cluster size of 8, the non-portable cluster size opt-in.

@@ -47,7 +47,8 @@ class sim_config(C.Structure):
         ("digest_capacity", C.c_uint32), ("timeout_ms", C.c_uint32), ("big_array_bytes", C.c_uint64),
         ("disable_stage3", C.c_uint32), ("seed_partition", C.c_uint32), ("lowering", C.c_uint32),
         ("task_order", C.c_uint32), ("phase_samples", C.c_uint32), ("wave_groups", C.c_uint32),
-        ("cluster_size", C.c_uint32), ("partitioner", C.c_uint32), ("reserved", C.c_uint32 * 2),
+        ("cluster_size", C.c_uint32), ("partitioner", C.c_uint32), ("chain", C.c_uint32),
+        ("reserved", C.c_uint32 * 1),
     ]
 
 

@@ -12,10 +12,11 @@ from paper_2403_04714_gb300 import netgen, sim
 from test_oracle_bruteforce import random_tiny_circuit
 
 
-def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False, cluster=None, partitioner="slb"):
-    extra = {"partitioner": partitioner}
+def run_compare(text, mode, cycles, target=0, seed_partition=0, shuffle=False, cluster=None, partitioner="slb",
+                chain=0):
+    extra = {"partitioner": partitioner, "chain": chain}
     if cluster:
-        extra = dict(cluster_size=cluster[0], warps_per_cta=cluster[1])
+        extra = dict(cluster_size=cluster[0], warps_per_cta=cluster[1], chain=chain)
     base_mode = mode.replace("_compact", "").replace("_cluster", "")
     nl = sim.Netlist(text, mode=base_mode, target_processes=target, seed_partition=seed_partition, **extra)
     emu = Emu(text, nl, mode, seed=42, inst=0)
@@ -76,3 +77,21 @@ def test_cluster_flat_netlist_with_rams():
     text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
     for C, W, target in ((4, 2, 16), (4, 2, 8), (8, 4, 40)):
         run_compare(text, "lane_op_cluster", 20, target=target, shuffle=True, cluster=(C, W))
+
+
+# Operator chains (sim_config.chain = 2): a lane runs a dependent pair of
+# operators in one step; the emulator reads a chain step as two rows.
+@pytest.mark.parametrize("seed", range(6))
+def test_chained_random_circuits_with_memory(seed):
+    text = random_tiny_circuit(seed).to_text()
+    for target in (1, 2, 4):
+        run_compare(text, "lane_op_compact", 25, target=target, shuffle=True, chain=2)
+    run_compare(text, "lane_op_cluster", 20, target=2, shuffle=True, cluster=(2, 1), chain=2)
+
+
+def test_chained_tiny_and_flat():
+    run_compare(open(netgen.cached_netlist("tiny")).read(), "lane_op_compact", 40, shuffle=True, chain=2)
+    run_compare(open(netgen.cached_netlist("tiny")).read(), "lane_op_cluster", 30, target=16, shuffle=True,
+                cluster=(4, 2), chain=2)
+    text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
+    run_compare(text, "lane_op_compact", 30, target=16, shuffle=True, chain=2)

@@ -13,10 +13,10 @@ ALU = set(range(5, 18))
 D_MUX, D_SLICE = 15, 16
 D_STR, D_WREC, D_COMMIT, D_LDM, D_STX = 18, 19, 20, 21, 22
 LEAVES = {D_LDR, D_LDI, D_CONST, D_LDM}
-GENERIC, LEAF = 1 << 31, 1 << 30
+GENERIC, LEAF, CHAIN = 1 << 31, 1 << 30, 1 << 29
 
 
-def reads(d):
+def _reads(d):
     op = int(d["op"])
     if op in ALU:
         if op == D_MUX:
@@ -35,6 +35,44 @@ def writes(d):
     return int(d["dst"]) if int(d["op"]) in ALU or int(d["op"]) in LEAVES | {D_MEMRD} else None
 
 
+def check_chain_step(p, b, e, step, valid, slots):
+    """A chain step: n first operators, then n second operators (D_NOP where
+    a lane has none).  A second operator's operands flagged in imm bits 0/1/2
+    name its own lane's first result; every other operand was written by an
+    earlier step; no slot is written twice or read and written in the step."""
+    assert e & GENERIC and len(step) % 2 == 0 and len(step) <= 64, (p, b)
+    n = len(step) // 2
+    firsts, seconds = step[:n], step[n:]
+    assert all(int(d["op"]) in ALU for d in firsts), (p, b)
+    assert all(int(d["op"]) in ALU or int(d["op"]) == 0 for d in seconds), (p, b)
+    dsts = [int(d["dst"]) for d in firsts] + [int(d["dst"]) for d in seconds if int(d["op"]) != 0]
+    assert len(dsts) == len(set(dsts)), (p, b, "slot written twice in one step")
+    reads = set()
+    for d in firsts:
+        for s in _reads(d):
+            assert s in valid, (p, b, "operand slot read before any write")
+            reads.add(s)
+    chained = 0
+    for f, d in zip(firsts, seconds):
+        if int(d["op"]) == 0:
+            continue
+        flags = int(d["imm"])
+        names = ["a", "b", "c"][:len(_reads(d))]
+        assert flags and not flags >> len(names), (p, b, "a second operator must use its lane's first result")
+        for k, name in enumerate(names):
+            if flags >> k & 1:
+                assert int(d[name]) == int(f["dst"]), (p, b, "chained operand names the first result's slot")
+                chained += 1
+            else:
+                assert int(d[name]) in valid, (p, b, "operand slot read before any write")
+                reads.add(int(d[name]))
+    assert chained > 0
+    assert not reads & set(dsts), (p, b, "slot read and written in one step")
+    for s in dsts:
+        assert s < int(slots[p])
+        valid[s] = b
+
+
 def check_programs(nl):
     words, off, size = nl.table("c_words"), nl.table("c_off"), nl.table("c_size")
     slots = nl.table("s_slots")
@@ -51,8 +89,18 @@ def check_programs(nl):
             first_expected += cnt
             step = ins[first:first + cnt]
             ops = [int(d["op"]) for d in step]
+            if e & CHAIN:
+                check_chain_step(p, b, e, step, valid, slots)
+                continue
             if not e & GENERIC:
                 assert all(o in ALU for o in ops), (p, b, "operator step holds another kind")
+                # bits 24-27: the operator groups the step uses (the interpreter
+                # evaluates only those): add/sub/and/or/xor, mul, shifts, compares/mux
+                groups = {o: g for g, kinds in enumerate(((5, 6, 8, 9, 10), (7,), (11, 12, 16, 17), (13, 14, 15)))
+                          for o in kinds}
+                assert (e >> 24) & 0xF == sum({1 << groups[o] for o in ops}), (p, b, "operator groups")
+            else:
+                assert (e >> 24) & 0xF == 0, (p, b)
             if e & LEAF:
                 assert all(o in LEAVES for o in ops) and cnt <= 128, (p, b)
             else:
@@ -61,7 +109,7 @@ def check_programs(nl):
             assert len(dsts) == len(set(dsts)), (p, b, "slot written twice in one step")
             step_reads = set()
             for d in step:
-                for s in reads(d):
+                for s in _reads(d):
                     assert s in valid, (p, b, "operand slot read before any write")
                     step_reads.add(s)
             assert not step_reads & set(dsts), (p, b, "slot read and written in one step")
@@ -80,3 +128,15 @@ def test_programs_with_memories_and_clusters():
     text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
     check_programs(sim.Netlist(text, mode="lane_op", target_processes=16))
     check_programs(sim.Netlist(text, mode="lane_op", cluster_size=4, warps_per_cta=2, target_processes=16))
+
+
+@pytest.mark.parametrize("name", ["tiny", "mid"])
+def test_chained_programs_of_the_workloads(name):
+    text = open(netgen.cached_netlist(name)).read()
+    check_programs(sim.Netlist(text, mode="lane_op", chain=2))
+    check_programs(sim.Netlist(text, mode="lane_op", chain=2, cluster_size=4, warps_per_cta=4))
+
+
+def test_chained_programs_with_memories():
+    text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
+    check_programs(sim.Netlist(text, mode="lane_op", target_processes=16, chain=2))
