@@ -130,9 +130,9 @@ typedef struct sim_config {
     uint32_t partitioner;       /* SIM_PART_SLB (bottom-up merge, Sec. 5.1) or SIM_PART_HYPERGRAPH (k-way
                                  * hypergraph partition of the fibers minimising duplicated work, the
                                  * alternative strategy of Sec. 7) */
-    uint32_t chain;             /* LANE_OP shared-memory programs: 2 = a lane may run a dependent pair of operators
-                                 * in one step (the first result stays in a register), 0/1 = one dependence level
-                                 * per step */
+    uint32_t chain;             /* LANE_OP shared-memory programs: 2..4 = a lane may run a chain of up to this many
+                                 * dependent operators in one step (each result passed on in a register), 0/1 =
+                                 * one dependence level per step */
     uint32_t reserved[1];
 } sim_config;
 

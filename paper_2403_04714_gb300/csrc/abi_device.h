@@ -45,22 +45,21 @@ struct DIns {
 // such a step may hold up to kLeafStepMax instructions, four per lane.
 constexpr uint32_t kStepGeneric = 1u << 31;
 constexpr uint32_t kStepLeaf = 1u << 30;
-// A chain step (also kStepGeneric) holds count first operators, one per
-// lane, then count second operators (D_NOP where a lane has none); a second
-// operator's imm bits 0/1/2 mark operands a/b/c taken from the lane's first
-// result (their slot fields name that result's slot).
+// A chain step (also kStepGeneric) holds R rows (bits 24-27 of the step
+// word) of n = count / R operators: lane i runs the operators i, n + i, ...
+// one after another, without a warp barrier between them (a lane that has
+// fewer holds D_NOP in its last rows).  An operator's imm bits 0/1/2 mark
+// operands a/b/c that are the result of the lane's previous operator in the
+// step, taken from a register (their slot fields name that result's slot,
+// so the rows also read as sequential steps).
 constexpr uint32_t kStepChain = 1u << 29;
+constexpr uint32_t kStepRowsShift = 24;
+constexpr uint32_t kStepRowsMask = 0xfu;
+constexpr uint32_t kChainMax = 4;
 constexpr uint32_t kStepCountMask = 0xffu;
 constexpr uint32_t kLeafStepMax = 128;
 
-// Operator steps also carry, in bits 24-27, the set of operator groups their
-// instructions use, so the interpreter evaluates only those groups:
-//   group 0: add, sub, and, or, xor     group 1: mul
-//   group 2: shl, shr, slice, concat    group 3: eq, lt, mux
-// kOpGroups holds the group of operator k = op - D_ADD in bits 2k..2k+1.
-constexpr uint32_t kStepGroupShift = 24;
-constexpr uint32_t kStepGroupMask = 0xfu;
-constexpr uint32_t kOpGroups = 0x2bfa010u;
+
 
 // Program tables of one lowered netlist (device pointers).
 struct DevProg {

@@ -1441,11 +1441,7 @@ int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words
     words[base] = nb;
     uint32_t first = 0;
     for (uint32_t b = 0; b < nb; b++) {
-        uint32_t groups = 0;      // operator groups of an operator step
-        if (!(steps[b].flags & kStepGeneric))
-            for (const DIns& d : steps[b].ins) groups |= 1u << ((kOpGroups >> (2 * (d.op - D_ADD))) & 3u);
-        words[base + 1 + b] = first | (uint32_t(steps[b].ins.size()) << 16) | steps[b].flags |
-                              (groups << kStepGroupShift);
+        words[base + 1 + b] = first | (uint32_t(steps[b].ins.size()) << 16) | steps[b].flags;
         for (const DIns& d : steps[b].ins) {
             uint32_t w4[4];
             memcpy(w4, &d, 16);
@@ -1461,30 +1457,29 @@ int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words
 }
 
 
-// Compact program with operator chains (sim_config.chain = 2).  Operators
-// are scheduled in dependence order; an operator whose operands are all
-// ready before the step of one of them, d, and d is the only operator of its
-// lane in that step, runs in the same step on d's lane right after it,
-// taking d's result from a register instead of from the slot after a warp
-// barrier.  Each such step (kStepChain) holds the lanes' first operators,
-// then their second operators (D_NOP where a lane has none); a second
-// operator's imm bits 0/1/2 mark operands a/b/c that come from the lane's
-// first result, whose slot field names that result's slot (so the steps
-// still read as two sequential rows).  Memory reads never chain.  Slots are
-// allocated over the compact steps (a value lives from its step to the end
-// of the step of its last use).
+// Compact program with operator chains (sim_config.chain = K, 2..4).
+// Operators are scheduled in dependence order; an operator whose operands are
+// all ready before the step of one of them, d, or come from d's lane in that
+// step, runs in d's step right after d on the same lane (up to K operators
+// per lane), taking d's result from a register instead of from the slot
+// after a warp barrier (results from earlier in the lane's chain are read
+// back from their slots by the same thread).  A step with chains (kStepChain)
+// holds R rows of its n lanes' operators (D_NOP where a lane's chain is
+// shorter); imm bits 0/1/2 mark operands a/b/c that are the previous result
+// of the lane.  Memory reads never chain.  Slots are allocated over the
+// compact steps (a value lives from its step to the end of the step of its
+// last use).
 template <class MakeIns, class Operands>
 int chained_program(const Netlist& nl, const std::vector<Item>& items, const std::vector<int32_t>& local, size_t n_local,
-                    MakeIns& make_ins, Operands& operands, Lowered& out, size_t p, std::string& err) {
+                    MakeIns& make_ins, Operands& operands, Lowered& out, size_t p, uint32_t K, std::string& err) {
     std::vector<size_t> commits, leaves, opers, sinks;
     for (size_t i = 0; i < items.size(); i++)
         (items[i].phase == 0 ? commits : items[i].phase == 1 ? leaves : items[i].phase == 2 ? opers : sinks).push_back(i);
     const size_t no = opers.size();
     std::vector<int32_t> op_of_local(n_local, -1);
     for (size_t k = 0; k < no; k++) op_of_local[local[items[opers[k]].id]] = int32_t(k);
-    std::vector<int32_t> ostep(no, 0), olane(no, 0), opos(no, 0);
-    struct LaneOps { int32_t first = -1, second = -1; };
-    std::vector<std::vector<LaneOps>> lanes;
+    std::vector<int32_t> ostep(no, 0), olane(no, 0);
+    std::vector<std::vector<std::vector<int32_t>>> lanes;   // step -> lane -> operators in order
     std::vector<uint8_t> has_memrd, has_chain;
     std::vector<int32_t> deps;
     for (size_t k = 0; k < no; k++) {
@@ -1497,19 +1492,17 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
         int32_t s = 0;
         for (int32_t q : deps) s = std::max(s, ostep[q] + 1);
         bool placed = false;
-        if (!memrd && s > 0)
+        if (!memrd && s > 0 && !has_memrd[s - 1])
             for (int32_t d : deps) {
-                if (ostep[d] != s - 1 || opos[d] != 0) continue;
-                if (has_memrd[s - 1] || nl.nodes[items[opers[d]].id].op == OP_MEMRD) continue;
-                LaneOps& L = lanes[s - 1][olane[d]];
-                if (L.second >= 0) continue;
+                if (ostep[d] != s - 1 || nl.nodes[items[opers[d]].id].op == OP_MEMRD) continue;
+                auto& L = lanes[s - 1][olane[d]];
+                if (L.back() != d || L.size() >= K) continue;
                 bool ok = true;
-                for (int32_t q : deps) ok &= q == d || ostep[q] < s - 1;
+                for (int32_t q : deps) ok &= ostep[q] < s - 1 || olane[q] == olane[d];
                 if (!ok) continue;
-                L.second = int32_t(k);
+                L.push_back(int32_t(k));
                 ostep[k] = s - 1;
                 olane[k] = olane[d];
-                opos[k] = 1;
                 has_chain[s - 1] = 1;
                 placed = true;
                 break;
@@ -1523,12 +1516,10 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
         }
         ostep[k] = s;
         olane[k] = int32_t(lanes[s].size());
-        opos[k] = 0;
-        lanes[s].push_back(LaneOps{int32_t(k), -1});
+        lanes[s].push_back({int32_t(k)});
         if (memrd) has_memrd[s] = 1;
     }
-    // steps as lists of item indices (second operators after the first ones;
-    // -1 = a lane without a second operator)
+    // steps as lists of item indices (-1 = D_NOP of a shorter chain)
     struct PStep { uint32_t flags; std::vector<int64_t> its; uint32_t lanes; };
     std::vector<PStep> ps;
     for (size_t k = 0; k < commits.size(); k += 32) {
@@ -1542,11 +1533,12 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
         ps.push_back(std::move(st));
     }
     for (size_t s = 0; s < lanes.size(); s++) {
-        PStep st{has_memrd[s] ? kStepGeneric : has_chain[s] ? (kStepGeneric | kStepChain) : 0u, {}, 0};
-        for (auto& L : lanes[s]) st.its.push_back(int64_t(opers[L.first]));
-        if (has_chain[s])
-            for (auto& L : lanes[s]) st.its.push_back(L.second >= 0 ? int64_t(opers[L.second]) : -1);
-        st.lanes = uint32_t(lanes[s].size());
+        uint32_t rows = 1;
+        for (auto& L : lanes[s]) rows = std::max<uint32_t>(rows, uint32_t(L.size()));
+        PStep st{has_memrd[s] ? kStepGeneric : rows > 1 ? (kStepGeneric | kStepChain | (rows << kStepRowsShift)) : 0u,
+                 {}, uint32_t(lanes[s].size())};
+        for (uint32_t r = 0; r < rows; r++)
+            for (auto& L : lanes[s]) st.its.push_back(r < L.size() ? int64_t(opers[L[r]]) : -1);
         ps.push_back(std::move(st));
     }
     for (size_t k = 0; k < sinks.size(); k += 32) {
@@ -1555,14 +1547,10 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
         ps.push_back(std::move(st));
     }
     // value lifetimes over the compact steps
-    std::vector<int32_t> last(n_local, -1), def_step(n_local, -1);
+    std::vector<int32_t> last(n_local, -1);
     for (size_t b = 0; b < ps.size(); b++)
-        for (int64_t i : ps[b].its) {
-            if (i < 0) continue;
-            const Item& it = items[size_t(i)];
-            if (it.kind == 0) def_step[local[it.id]] = int32_t(b);
-            operands(it, [&](int32_t n) { last[local[n]] = std::max(last[local[n]], int32_t(b)); });
-        }
+        for (int64_t i : ps[b].its)
+            if (i >= 0) operands(items[size_t(i)], [&](int32_t n) { last[local[n]] = std::max(last[local[n]], int32_t(b)); });
     std::vector<uint16_t> slot(n_local, kNoSlot);
     SlotAlloc A;
     std::vector<std::vector<uint16_t>> release(ps.size() + 1);
@@ -1577,6 +1565,7 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
         }
         CStep st;
         st.flags = ps[b].flags;
+        const uint32_t n = ps[b].lanes;
         for (size_t j = 0; j < ps[b].its.size(); j++) {
             const int64_t i = ps[b].its[j];
             if (i < 0) {
@@ -1586,16 +1575,14 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
                 continue;
             }
             DIns d = make_ins(items[size_t(i)], slot);
-            if ((ps[b].flags & kStepChain) && j >= ps[b].lanes) {
-                // operands produced by this lane's first operator come from its register
-                const int64_t f = ps[b].its[j - ps[b].lanes];
-                const int32_t first_local = local[items[size_t(f)].id];
-                const Node& n = nl.nodes[items[size_t(i)].id];
-                auto from_first = [&](int32_t node) { return node >= 0 && local[node] == first_local; };
-                const bool two = n.op != OP_SLICE;
-                if (from_first(n.a)) d.imm |= 1u;
-                if (two && from_first(n.b)) d.imm |= 2u;
-                if (n.op == OP_MUX && from_first(n.c)) d.imm |= 4u;
+            if ((ps[b].flags & kStepChain) && j >= n) {
+                // operands that are the lane's previous result come from its register
+                const int32_t prev = local[items[size_t(ps[b].its[j - n])].id];
+                const Node& nd = nl.nodes[items[size_t(i)].id];
+                auto is_prev = [&](int32_t node) { return local[node] == prev; };
+                if (is_prev(nd.a)) d.imm |= 1u;
+                if (nd.op != OP_SLICE && is_prev(nd.b)) d.imm |= 2u;
+                if (nd.op == OP_MUX && is_prev(nd.c)) d.imm |= 4u;
             }
             st.ins.push_back(d);
         }
@@ -1607,7 +1594,6 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
     int rc = append_program(steps, out.c_words, err);
     if (rc) return rc;
     out.c_size[p] = uint32_t(out.c_words.size()) - out.c_off[p];
-    (void)def_step;
     return SIM_OK;
 }
 
@@ -1803,7 +1789,7 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
             if (A.next > 0xfff0) { err = "process needs too many value slots"; return SIM_ERR_CAPACITY; }
         }
         if (chain >= 2) {
-            int rc = chained_program(nl, items, local, nodes.size(), make_ins, operands, out, p, err);
+            int rc = chained_program(nl, items, local, nodes.size(), make_ins, operands, out, p, chain, err);
             if (rc) return rc;
         } else {
             // compact copy: the occupied lanes of each row; up to four rows of
@@ -1929,7 +1915,7 @@ std::vector<CStep> read_steps(const Lowered& low, size_t p) {
     std::vector<CStep> steps(nb);
     for (uint32_t b = 0; b < nb; b++) {
         const uint32_t e = w[1 + b], first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        steps[b].flags = e & (kStepGeneric | kStepLeaf | kStepChain);
+        steps[b].flags = e & (kStepGeneric | kStepLeaf | kStepChain | (kStepRowsMask << kStepRowsShift));
         steps[b].ins.assign(ins + first, ins + first + cnt);
     }
     return steps;
@@ -2174,7 +2160,8 @@ int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_
         low.s_off[p] = uint32_t(low.s_ins.size() / 32);
         for (const auto& st : steps[p]) {
             // a chain step reads as two rows: the first operators, then the second ones
-            const size_t row = (st.flags & kStepChain) ? st.ins.size() / 2 : 32;
+            const size_t row = (st.flags & kStepChain) ? st.ins.size() / ((st.flags >> kStepRowsShift) & kStepRowsMask)
+                                                       : 32;
             for (size_t k = 0; k < std::max<size_t>(1, st.ins.size()); k += row) {
                 const size_t base = low.s_ins.size();
                 low.s_ins.resize(base + 32, DIns{});

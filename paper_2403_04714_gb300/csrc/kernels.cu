@@ -413,19 +413,21 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
             const Dec d = decode(ins[on ? first + lane : first]);
             sl[on ? d.dst : dummy] = eval_op<VAR>(d, sl[d.a], sl[d.b], sl[d.c]);
         } else if (e & kStepChain) {
-            // each lane: its first operator, then a second one that may take
-            // the first result from the register (imm bits 0/1/2 for a/b/c)
-            const uint32_t n = cnt >> 1;
+            // rows of operators run one after another by each lane (no warp
+            // barrier between them); imm bits 0/1/2 take operands a/b/c from
+            // the lane's previous result
+            const uint32_t rows = (e >> kStepRowsShift) & kStepRowsMask, n = cnt / rows;
             const bool on = lane < n;
-            const uint32_t i1 = on ? first + lane : first;
-            const Dec d1 = decode(ins[i1]);
-            const Dec d2 = decode(ins[i1 + n]);
-            const uint64_t r1 = eval_op<VAR>(d1, sl[d1.a], sl[d1.b], sl[d1.c]);
-            sl[on ? d1.dst : dummy] = r1;
-            const uint64_t a2 = (d2.imm & 1u) ? r1 : sl[d2.a];
-            const uint64_t b2 = (d2.imm & 2u) ? r1 : sl[d2.b];
-            const uint64_t c2 = (d2.imm & 4u) ? r1 : sl[d2.c];
-            sl[on && d2.op != D_NOP ? d2.dst : dummy] = eval_op<VAR>(d2, a2, b2, c2);
+            uint32_t i = on ? first + lane : first;
+            uint64_t r = 0;
+            for (uint32_t j = 0; j < rows; j++, i += n) {
+                const Dec d = decode(ins[i]);
+                const uint64_t a = (d.imm & 1u) ? r : sl[d.a];
+                const uint64_t bb = (d.imm & 2u) ? r : sl[d.b];
+                const uint64_t c = (d.imm & 4u) ? r : sl[d.c];
+                r = eval_op<VAR>(d, a, bb, c);
+                sl[on && d.op != D_NOP ? d.dst : dummy] = r;
+            }
         } else if (e & kStepLeaf) {
             // up to four leaves per lane, every load in flight before the
             // first value is stored; idle lanes write the spare slot

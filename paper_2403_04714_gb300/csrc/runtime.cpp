@@ -292,7 +292,7 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
             rc = partition(h->nl, pc, h->part, err);
             if (rc) return set_err(rc, err);
         }
-        if (h->cfg.chain > 2) return set_err(SIM_ERR_BADARG, "chain must be 0, 1 or 2");
+        if (h->cfg.chain > kChainMax) return set_err(SIM_ERR_BADARG, "chain must be 0..4");
         rc = lower(h->nl, h->part, h->low, err, h->cfg.chain);
         if (rc) return set_err(rc, err);
         if (h->cfg.cluster_size) {

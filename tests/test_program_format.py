@@ -36,38 +36,42 @@ def writes(d):
 
 
 def check_chain_step(p, b, e, step, valid, slots):
-    """A chain step: n first operators, then n second operators (D_NOP where
-    a lane has none).  A second operator's operands flagged in imm bits 0/1/2
-    name its own lane's first result; every other operand was written by an
-    earlier step; no slot is written twice or read and written in the step."""
-    assert e & GENERIC and len(step) % 2 == 0 and len(step) <= 64, (p, b)
-    n = len(step) // 2
-    firsts, seconds = step[:n], step[n:]
-    assert all(int(d["op"]) in ALU for d in firsts), (p, b)
-    assert all(int(d["op"]) in ALU or int(d["op"]) == 0 for d in seconds), (p, b)
-    dsts = [int(d["dst"]) for d in firsts] + [int(d["dst"]) for d in seconds if int(d["op"]) != 0]
+    """A chain step: R rows (bits 24-27) of n operators; lane i runs the
+    operators i, n + i, ... in order (D_NOP after the end of its chain).  An
+    operand flagged in imm bits 0/1/2 names the slot of the lane's previous
+    operator; every other operand was written by an earlier step or earlier
+    in the lane's own chain; no slot is written twice, and no slot written in
+    the step is read there by another lane."""
+    rows = (e >> 24) & 0xF
+    assert e & GENERIC and rows >= 2 and len(step) % rows == 0 and len(step) // rows <= 32, (p, b)
+    n = len(step) // rows
+    grid = [step[r * n:(r + 1) * n] for r in range(rows)]
+    assert all(int(d["op"]) in ALU for d in grid[0]), (p, b)
+    dsts = [int(d["dst"]) for row in grid for d in row if int(d["op"]) != 0]
     assert len(dsts) == len(set(dsts)), (p, b, "slot written twice in one step")
-    reads = set()
-    for d in firsts:
-        for s in _reads(d):
-            assert s in valid, (p, b, "operand slot read before any write")
-            reads.add(s)
     chained = 0
-    for f, d in zip(firsts, seconds):
-        if int(d["op"]) == 0:
-            continue
-        flags = int(d["imm"])
-        names = ["a", "b", "c"][:len(_reads(d))]
-        assert flags and not flags >> len(names), (p, b, "a second operator must use its lane's first result")
-        for k, name in enumerate(names):
-            if flags >> k & 1:
-                assert int(d[name]) == int(f["dst"]), (p, b, "chained operand names the first result's slot")
-                chained += 1
-            else:
-                assert int(d[name]) in valid, (p, b, "operand slot read before any write")
-                reads.add(int(d[name]))
+    for lane in range(n):
+        own = set()                     # slots this lane wrote earlier in the step
+        ended = False
+        for r in range(rows):
+            d = grid[r][lane]
+            if int(d["op"]) == 0:
+                ended = True
+                continue
+            assert int(d["op"]) in ALU and not ended, (p, b, "chains are contiguous operator runs")
+            flags = int(d["imm"]) if r else 0
+            names = ["a", "b", "c"][:len(_reads(d))]
+            assert not flags >> len(names), (p, b)
+            for k, name in enumerate(names):
+                sl = int(d[name])
+                if flags >> k & 1:
+                    assert sl == int(grid[r - 1][lane]["dst"]), (p, b, "chained operand names the previous result")
+                    chained += 1
+                else:
+                    assert sl in valid or sl in own, (p, b, "operand slot read before any write")
+                    assert sl in own or sl not in dsts, (p, b, "slot written in this step read by another lane")
+            own.add(int(d["dst"]))
     assert chained > 0
-    assert not reads & set(dsts), (p, b, "slot read and written in one step")
     for s in dsts:
         assert s < int(slots[p])
         valid[s] = b
@@ -94,13 +98,6 @@ def check_programs(nl):
                 continue
             if not e & GENERIC:
                 assert all(o in ALU for o in ops), (p, b, "operator step holds another kind")
-                # bits 24-27: the operator groups the step uses (the interpreter
-                # evaluates only those): add/sub/and/or/xor, mul, shifts, compares/mux
-                groups = {o: g for g, kinds in enumerate(((5, 6, 8, 9, 10), (7,), (11, 12, 16, 17), (13, 14, 15)))
-                          for o in kinds}
-                assert (e >> 24) & 0xF == sum({1 << groups[o] for o in ops}), (p, b, "operator groups")
-            else:
-                assert (e >> 24) & 0xF == 0, (p, b)
             if e & LEAF:
                 assert all(o in LEAVES for o in ops) and cnt <= 128, (p, b)
             else:
@@ -133,8 +130,9 @@ def test_programs_with_memories_and_clusters():
 @pytest.mark.parametrize("name", ["tiny", "mid"])
 def test_chained_programs_of_the_workloads(name):
     text = open(netgen.cached_netlist(name)).read()
-    check_programs(sim.Netlist(text, mode="lane_op", chain=2))
-    check_programs(sim.Netlist(text, mode="lane_op", chain=2, cluster_size=4, warps_per_cta=4))
+    for k in (2, 3, 4):
+        check_programs(sim.Netlist(text, mode="lane_op", chain=k))
+    check_programs(sim.Netlist(text, mode="lane_op", chain=3, cluster_size=4, warps_per_cta=4))
 
 
 def test_chained_programs_with_memories():
