@@ -130,8 +130,8 @@ typedef struct sim_config {
     uint32_t partitioner;       /* SIM_PART_SLB (bottom-up merge, Sec. 5.1) or SIM_PART_HYPERGRAPH (k-way
                                  * hypergraph partition of the fibers minimising duplicated work, the
                                  * alternative strategy of Sec. 7) */
-    uint32_t chain;             /* LANE_OP shared-memory programs: 2..4 = a lane may run a chain of up to this many
-                                 * dependent operators in one step (each result passed on in a register), 0/1 =
+    uint32_t chain;             /* LANE_OP shared-memory programs: 2 = a lane may run a dependent pair of operators
+                                 * in one step (the first result passed on in a register; the default), 0/1 =
                                  * one dependence level per step */
     uint32_t reserved[1];
 } sim_config;
@@ -155,7 +155,8 @@ typedef struct sim_netlist_info {
 typedef struct sim_netlist sim_netlist;
 typedef struct sim_batch sim_batch;
 
-/* Fill cfg with defaults (AUTO mode, persistent kernel, digests off). */
+/* Fill cfg with defaults (AUTO mode, persistent kernel, digests off, operator
+ * pairs chained). */
 void sim_config_default(sim_config *cfg);
 
 /* Parse, check, partition (fibers -> SLB processes, paper Sec. 5.1) and lower

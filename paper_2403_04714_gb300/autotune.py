@@ -44,11 +44,14 @@ def default_candidates(n_inst: int, sms: int = 152):
     if n_inst >= 32:
         return [dict(mode="lane_inst", lowering="generated", warps_per_cta=w, task_order=o)
                 for w in (8, 4) for o in ("process_major", "group_major")]
-    cands = [dict(mode="lane_op", lowering="bytecode"),                      # adaptive: 4 or 8 per SM
-             dict(mode="lane_op", lowering="bytecode", warps_per_cta=8, target_processes=8 * sms),
-             dict(mode="lane_op", lowering="bytecode", warps_per_cta=3, target_processes=3 * sms)]
+    # operator pairs chained in one step (chain=2) measured faster on every
+    # geometry; the unchained adaptive geometry stays as the reference
+    cands = [dict(mode="lane_op", lowering="bytecode", chain=0),              # adaptive: 4 or 8 per SM
+             dict(mode="lane_op", lowering="bytecode", chain=2),
+             dict(mode="lane_op", lowering="bytecode", chain=2, warps_per_cta=8, target_processes=8 * sms),
+             dict(mode="lane_op", lowering="bytecode", chain=2, warps_per_cta=3, target_processes=3 * sms)]
     if n_inst == 1:     # cluster exchange (one instance): several clusters, and one 16-CTA cluster
-        cands += [dict(mode="lane_op", lowering="bytecode", cluster_size=c, warps_per_cta=w)
+        cands += [dict(mode="lane_op", lowering="bytecode", chain=2, cluster_size=c, warps_per_cta=w)
                   for c, w in ((4, 4), (6, 4), (2, 4), (16, 8))]
     return cands
 

@@ -45,17 +45,17 @@ struct DIns {
 // such a step may hold up to kLeafStepMax instructions, four per lane.
 constexpr uint32_t kStepGeneric = 1u << 31;
 constexpr uint32_t kStepLeaf = 1u << 30;
-// A chain step (also kStepGeneric) holds R rows (bits 24-27 of the step
-// word) of n = count / R operators: lane i runs the operators i, n + i, ...
-// one after another, without a warp barrier between them (a lane that has
-// fewer holds D_NOP in its last rows).  An operator's imm bits 0/1/2 mark
-// operands a/b/c that are the result of the lane's previous operator in the
-// step, taken from a register (their slot fields name that result's slot,
-// so the rows also read as sequential steps).
+// A chain step (also kStepGeneric) holds two rows (bits 24-27 of the step
+// word hold the row count) of n = count / 2 operators: lane i runs operator
+// i, then operator n + i, without a warp barrier between them (D_NOP in the
+// second row where a lane has one operator).  A second-row operator's imm
+// bits 0/1/2 mark operands a/b/c that are the lane's first result, taken
+// from a register (their slot fields name that result's slot, so the two
+// rows also read as sequential steps).
 constexpr uint32_t kStepChain = 1u << 29;
 constexpr uint32_t kStepRowsShift = 24;
 constexpr uint32_t kStepRowsMask = 0xfu;
-constexpr uint32_t kChainMax = 4;
+constexpr uint32_t kChainMax = 2;
 constexpr uint32_t kStepCountMask = 0xffu;
 constexpr uint32_t kLeafStepMax = 128;
 

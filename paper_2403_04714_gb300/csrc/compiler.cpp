@@ -1457,18 +1457,22 @@ int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words
 }
 
 
-// Compact program with operator chains (sim_config.chain = K, 2..4).
-// Operators are scheduled in dependence order; an operator whose operands are
-// all ready before the step of one of them, d, or come from d's lane in that
-// step, runs in d's step right after d on the same lane (up to K operators
-// per lane), taking d's result from a register instead of from the slot
-// after a warp barrier (results from earlier in the lane's chain are read
-// back from their slots by the same thread).  A step with chains (kStepChain)
-// holds R rows of its n lanes' operators (D_NOP where a lane's chain is
-// shorter); imm bits 0/1/2 mark operands a/b/c that are the previous result
-// of the lane.  Memory reads never chain.  Slots are allocated over the
-// compact steps (a value lives from its step to the end of the step of its
-// last use).
+// Compact program with operator chains (sim_config.chain = K = 2; the
+// scheduler takes any K, the interpreter runs pairs).  Operators are
+// scheduled in dependence order; an operator whose operands are all ready
+// before the step of one of them, d, or come from d's lane in that step, runs
+// in d's step right after d on the same lane (up to K operators per lane),
+// taking d's result from a register instead of from the slot after a warp
+// barrier.  A step with chains (kStepChain) holds R rows of its n lanes'
+// operators (D_NOP where a lane's chain is shorter); imm bits 0/1/2 mark
+// operands a/b/c that are the previous result of the lane.  Memory reads never
+// chain.  Slots are allocated over the compact steps (a value lives from its
+// step to the end of the step of its last use).
+// Measured on the mid netlist (one GB300, 4-CTA clusters): pairs take the
+// slowest process from 66 to 40 steps and the rate from 77-78k to 83-84k
+// cycles/s; chains of three or four (31 and 28 steps) gain nothing more,
+// because a step costs about as much to enter (instruction and operand loads,
+// store, warp barrier) as one more operator costs to evaluate.
 template <class MakeIns, class Operands>
 int chained_program(const Netlist& nl, const std::vector<Item>& items, const std::vector<int32_t>& local, size_t n_local,
                     MakeIns& make_ins, Operands& operands, Lowered& out, size_t p, uint32_t K, std::string& err) {

@@ -21,7 +21,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <cstdlib>
 #include <mutex>
 
 #include "../../include/sim.h"
@@ -235,32 +234,12 @@ static __device__ bool cluster_barrier(uint64_t* bars, uint32_t c, uint32_t C, u
 // ---------------------------------------------------------------------------
 // All 13 operators without branches: every candidate result is formed and the
 // opcode selects one, so lanes running different operators in one schedule
-// step follow a single instruction path (no serialised divergent paths).
+// step follow a single instruction path (no serialised divergent paths).  One
+// left and one right shift serve the four shift-like operators (the amount is
+// b for shl/shr and the static x for slice/concat), and add/sub share one
+// adder (b complemented with a carry in for sub); a select tree on the bits of
+// op - D_ADD (operators in enum order) picks the result in four levels.
 __device__ __forceinline__ uint64_t alu_select(uint32_t op, uint64_t a, uint64_t b, uint64_t c, uint32_t x) {
-    // every candidate result, then a select tree on the bits of op - D_ADD
-    // (operators in enum order): four dependent selects instead of a chain
-    // of twelve
-    const bool big = b >= 64;
-    const uint32_t s = uint32_t(b) & 63u;
-    const uint32_t k = op - D_ADD;
-    const bool k0 = k & 1u, k1 = k & 2u, k2 = k & 4u, k3 = k & 8u;
-    const uint64_t p0 = k0 ? a - b : a + b;                                  // ADD, SUB
-    const uint64_t p1 = k0 ? (a & b) : a * b;                                // MUL, AND
-    const uint64_t p2 = k0 ? (a ^ b) : (a | b);                              // OR, XOR
-    const uint64_t p3 = big ? 0ull : (k0 ? a >> s : a << s);                 // SHL, SHR
-    const uint64_t p4 = k0 ? (uint64_t)(a < b) : (uint64_t)(a == b);         // EQ, LT
-    const uint64_t p5 = k0 ? (a >> (x & 63u)) : (a != 0 ? b : c);            // MUX, SLICE
-    const uint64_t p6 = (a << (x & 63u)) | b;                                // CONCAT
-    const uint64_t q0 = k1 ? p1 : p0, q1 = k1 ? p3 : p2, q2 = k1 ? p5 : p4;
-    const uint64_t r0 = k2 ? q1 : q0, r1 = k2 ? p6 : q2;
-    return k3 ? r1 : r0;
-}
-
-// The same selection with fewer instructions: one left and one right shift
-// serve all four shift-like operators (the amount is b for shl/shr and the
-// static x for slice/concat), and add/sub share one adder (b complemented,
-// carry in, for sub).
-__device__ __forceinline__ uint64_t alu_select_lean(uint32_t op, uint64_t a, uint64_t b, uint64_t c, uint32_t x) {
     const uint32_t k = op - D_ADD;
     const bool k0 = k & 1u, k1 = k & 2u, k2 = k & 4u, k3 = k & 8u;
     const bool dyn = (k >> 1) == 3u;                                         // SHL, SHR
@@ -380,9 +359,8 @@ __device__ void task_lane_op(const DevProg& P, const DevState& S, uint32_t p, ui
 }
 
 // Result of one operator instruction, reduced to its width.
-template <int VAR>
 __device__ __forceinline__ uint64_t eval_op(const Dec& d, uint64_t a, uint64_t b, uint64_t c) {
-    return (VAR == 1 ? alu_select_lean(d.op, a, b, c, d.x) : alu_select(d.op, a, b, c, d.x)) & wmask(d.w);
+    return alu_select(d.op, a, b, c, d.x) & wmask(d.w);
 }
 
 // Program resident in shared memory: `prog` holds the step count, the step
@@ -391,8 +369,7 @@ __device__ __forceinline__ uint64_t eval_op(const Dec& d, uint64_t a, uint64_t b
 // lanes past the step's count repeat its first instruction and write the
 // spare slot `dummy` (the last word of the warp's slot region), which no
 // instruction reads.
-// VAR 1: operator steps use the lean evaluator.
-template <bool DIGEST, int VAR>
+template <bool DIGEST>
 __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t,
                                  bool pending, uint64_t* __restrict__ sl, const uint32_t* __restrict__ prog,
                                  uint32_t lane, uint32_t dummy, const uint64_t* mir_cur = nullptr,
@@ -411,23 +388,22 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
             // operator step: all 32 lanes, no branch (idle lanes write the spare slot)
             const bool on = lane < cnt;
             const Dec d = decode(ins[on ? first + lane : first]);
-            sl[on ? d.dst : dummy] = eval_op<VAR>(d, sl[d.a], sl[d.b], sl[d.c]);
+            sl[on ? d.dst : dummy] = eval_op(d, sl[d.a], sl[d.b], sl[d.c]);
         } else if (e & kStepChain) {
-            // rows of operators run one after another by each lane (no warp
-            // barrier between them); imm bits 0/1/2 take operands a/b/c from
-            // the lane's previous result
-            const uint32_t rows = (e >> kStepRowsShift) & kStepRowsMask, n = cnt / rows;
+            // two rows: each lane's first operator, then its second one (no
+            // warp barrier between them); imm bits 0/1/2 take operands a/b/c
+            // of the second from the first result
+            const uint32_t n = cnt >> 1;
             const bool on = lane < n;
-            uint32_t i = on ? first + lane : first;
-            uint64_t r = 0;
-            for (uint32_t j = 0; j < rows; j++, i += n) {
-                const Dec d = decode(ins[i]);
-                const uint64_t a = (d.imm & 1u) ? r : sl[d.a];
-                const uint64_t bb = (d.imm & 2u) ? r : sl[d.b];
-                const uint64_t c = (d.imm & 4u) ? r : sl[d.c];
-                r = eval_op<VAR>(d, a, bb, c);
-                sl[on && d.op != D_NOP ? d.dst : dummy] = r;
-            }
+            const uint32_t i1 = on ? first + lane : first;
+            const Dec d1 = decode(ins[i1]);
+            const Dec d2 = decode(ins[i1 + n]);
+            const uint64_t r1 = eval_op(d1, sl[d1.a], sl[d1.b], sl[d1.c]);
+            sl[on ? d1.dst : dummy] = r1;
+            const uint64_t a2 = (d2.imm & 1u) ? r1 : sl[d2.a];
+            const uint64_t b2 = (d2.imm & 2u) ? r1 : sl[d2.b];
+            const uint64_t c2 = (d2.imm & 4u) ? r1 : sl[d2.c];
+            sl[on && d2.op != D_NOP ? d2.dst : dummy] = eval_op(d2, a2, b2, c2);
         } else if (e & kStepLeaf) {
             // up to four leaves per lane, every load in flight before the
             // first value is stored; idle lanes write the spare slot
@@ -456,7 +432,7 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
 
-template <int MODE, bool DIGEST, int VAR>
+template <int MODE, bool DIGEST>
 __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -487,7 +463,7 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
             uint32_t off = 0;
             for (uint32_t p = warp; p < P.n_proc; p += tw) {
                 for (uint32_t g = 0; g < S.I; g++)
-                    task_lane_op_res<DIGEST, VAR>(P, S, p, g, t, pending, sl, prog + off, lane, A.slot_words - 1);
+                    task_lane_op_res<DIGEST>(P, S, p, g, t, pending, sl, prog + off, lane, A.slot_words - 1);
                 off += P.c_size[p];
             }
         } else {
@@ -516,7 +492,7 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
 // Mirror buffer t&1 holds cycle t's values; at launch it is filled from the
 // global state, which producers keep writing for readers in other clusters,
 // for the host and for the next launch.
-template <bool DIGEST, int VAR>
+template <bool DIGEST>
 __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
     __shared__ __align__(8) uint64_t cbar[2];
@@ -567,7 +543,7 @@ __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, Launc
         if (rec && threadIdx.x == 0) rec[0] = globaltimer_ns();
         if (p != kNoProc) {
             const uint32_t par = uint32_t(t & 1);
-            task_lane_op_res<DIGEST, VAR>(P, S, p, 0, t, pending, sl, prog, lane, slot_words - 1,
+            task_lane_op_res<DIGEST>(P, S, p, 0, t, pending, sl, prog, lane, slot_words - 1,
                                      mirror + (uint64_t)par * A.mirror_words,
                                      smem_addr(mirror + (uint64_t)(par ^ 1) * A.mirror_words));
         }
@@ -669,32 +645,12 @@ __global__ void k_state_digest(DevProg P, DevState S, uint32_t par, const uint64
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
-template <int MODE, bool DIGEST, int VAR>
-static void* kfun() { return reinterpret_cast<void*>(&k_cycles<MODE, DIGEST, VAR>); }
-
-// interpreter variant of the LANE_OP kernels (experiments: RTLSIM_VARIANT)
-static int variant() {
-    static const int v = [] {
-        const char* e = getenv("RTLSIM_VARIANT");
-        return e ? (atoi(e) & 3) : 0;
-    }();
-    return v;
-}
-
-template <bool DIGEST>
-static void* lane_op_fn() {
-    switch (variant()) {
-    case 1: return kfun<SIM_MODE_LANE_OP, DIGEST, 1>();
-    case 2: return kfun<SIM_MODE_LANE_OP, DIGEST, 2>();
-    case 3: return kfun<SIM_MODE_LANE_OP, DIGEST, 3>();
-    default: return kfun<SIM_MODE_LANE_OP, DIGEST, 0>();
-    }
-}
+template <int MODE, bool DIGEST>
+static void* kfun() { return reinterpret_cast<void*>(&k_cycles<MODE, DIGEST>); }
 
 static void* cycles_fn(int mode, bool digest) {
-    if (mode == SIM_MODE_LANE_INST)
-        return digest ? kfun<SIM_MODE_LANE_INST, true, 0>() : kfun<SIM_MODE_LANE_INST, false, 0>();
-    return digest ? lane_op_fn<true>() : lane_op_fn<false>();
+    if (mode == SIM_MODE_LANE_INST) return digest ? kfun<SIM_MODE_LANE_INST, true>() : kfun<SIM_MODE_LANE_INST, false>();
+    return digest ? kfun<SIM_MODE_LANE_OP, true>() : kfun<SIM_MODE_LANE_OP, false>();
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by every
@@ -728,17 +684,9 @@ cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
 }
 
-template <bool DIGEST>
-static void* cycles_cl_var() {
-    switch (variant()) {
-    case 1: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 1>);
-    case 2: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 2>);
-    case 3: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 3>);
-    default: return reinterpret_cast<void*>(&k_cycles_cl<DIGEST, 0>);
-    }
+static void* cycles_cl_fn(bool digest) {
+    return digest ? reinterpret_cast<void*>(&k_cycles_cl<true>) : reinterpret_cast<void*>(&k_cycles_cl<false>);
 }
-
-static void* cycles_cl_fn(bool digest) { return digest ? cycles_cl_var<true>() : cycles_cl_var<false>(); }
 
 // Shared-memory limit (monotonic, as for k_cycles) and, above the portable
 // cluster size of 8, the non-portable cluster size opt-in.

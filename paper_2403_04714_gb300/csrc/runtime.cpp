@@ -246,6 +246,7 @@ void sim_config_default(sim_config* cfg) {
     cfg->struct_size = sizeof(sim_config);
     cfg->mode = SIM_MODE_AUTO;
     cfg->kernel = SIM_KERNEL_PERSISTENT;
+    cfg->chain = 2;
     cfg->timeout_ms = 2000;
     cfg->big_array_bytes = 128 * 1024;
 }
@@ -292,7 +293,7 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
             rc = partition(h->nl, pc, h->part, err);
             if (rc) return set_err(rc, err);
         }
-        if (h->cfg.chain > kChainMax) return set_err(SIM_ERR_BADARG, "chain must be 0..4");
+        if (h->cfg.chain > kChainMax) return set_err(SIM_ERR_BADARG, "chain must be 0, 1 or 2");
         rc = lower(h->nl, h->part, h->low, err, h->cfg.chain);
         if (rc) return set_err(rc, err);
         if (h->cfg.cluster_size) {

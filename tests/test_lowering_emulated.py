@@ -84,9 +84,9 @@ def test_cluster_flat_netlist_with_rams():
 @pytest.mark.parametrize("seed", range(6))
 def test_chained_random_circuits_with_memory(seed):
     text = random_tiny_circuit(seed).to_text()
-    for target, k in ((1, 2), (2, 3), (4, 4)):
-        run_compare(text, "lane_op_compact", 25, target=target, shuffle=True, chain=k)
-    run_compare(text, "lane_op_cluster", 20, target=2, shuffle=True, cluster=(2, 1), chain=3)
+    for target in (1, 2, 4):
+        run_compare(text, "lane_op_compact", 25, target=target, shuffle=True, chain=2)
+    run_compare(text, "lane_op_cluster", 20, target=2, shuffle=True, cluster=(2, 1), chain=2)
 
 
 def test_chained_tiny_and_flat():
@@ -94,5 +94,5 @@ def test_chained_tiny_and_flat():
     run_compare(open(netgen.cached_netlist("tiny")).read(), "lane_op_cluster", 30, target=16, shuffle=True,
                 cluster=(4, 2), chain=2)
     text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
-    run_compare(text, "lane_op_compact", 30, target=16, shuffle=True, chain=3)
-    run_compare(text, "lane_op_compact", 30, target=8, shuffle=True, chain=4)
+    run_compare(text, "lane_op_compact", 30, target=16, shuffle=True, chain=2)
+    run_compare(text, "lane_op_compact", 30, target=8, shuffle=True, chain=2)

@@ -130,11 +130,12 @@ def test_programs_with_memories_and_clusters():
 @pytest.mark.parametrize("name", ["tiny", "mid"])
 def test_chained_programs_of_the_workloads(name):
     text = open(netgen.cached_netlist(name)).read()
-    for k in (2, 3, 4):
-        check_programs(sim.Netlist(text, mode="lane_op", chain=k))
-    check_programs(sim.Netlist(text, mode="lane_op", chain=3, cluster_size=4, warps_per_cta=4))
+    check_programs(sim.Netlist(text, mode="lane_op", chain=2))
+    check_programs(sim.Netlist(text, mode="lane_op", chain=2, cluster_size=4, warps_per_cta=4))
 
 
 def test_chained_programs_with_memories():
     text = netgen.gen_flat(7, n_ops=3000, n_regs=200, depth=15, n_inputs=6, rams=((4, 64), (3, 16))).to_text()
     check_programs(sim.Netlist(text, mode="lane_op", target_processes=16, chain=2))
+    with pytest.raises(sim.SimError):
+        sim.Netlist(text, mode="lane_op", chain=3)
