@@ -177,7 +177,9 @@ def mesh_row(stream, flush):
     text = open(netgen.cached_netlist("mesh"), "rb").read()
     out = {}
     for name, cfg in (("grid_barrier", dict(target_processes=1216, warps_per_cta=8)),
-                      ("cluster", dict(cluster_size=2, warps_per_cta=8))):
+                      ("cluster", dict(cluster_size=2, warps_per_cta=8)),
+                      ("cluster_pairs", dict(cluster_size=2, warps_per_cta=8, chain=2)),
+                      ("grid_barrier_w4_pairs", dict(target_processes=608, warps_per_cta=4, chain=2))):
         try:
             nl = sim.Netlist(text, mode="lane_op", **cfg)
             b = sim.Batch(nl, 1, seed=42, stream=stream)

@@ -131,8 +131,9 @@ typedef struct sim_config {
                                  * hypergraph partition of the fibers minimising duplicated work, the
                                  * alternative strategy of Sec. 7) */
     uint32_t chain;             /* LANE_OP shared-memory programs: 2 = a lane may run a dependent pair of operators
-                                 * in one step (the first result passed on in a register; the default), 0/1 =
-                                 * one dependence level per step */
+                                 * in one step (the first result passed on in a register), 0/1 = one dependence
+                                 * level per step (the default).  Pairs help when each SM sub-partition runs one
+                                 * warp and cost issue slots when warps share one. */
     uint32_t reserved[1];
 } sim_config;
 
@@ -155,8 +156,7 @@ typedef struct sim_netlist_info {
 typedef struct sim_netlist sim_netlist;
 typedef struct sim_batch sim_batch;
 
-/* Fill cfg with defaults (AUTO mode, persistent kernel, digests off, operator
- * pairs chained). */
+/* Fill cfg with defaults (AUTO mode, persistent kernel, digests off). */
 void sim_config_default(sim_config *cfg);
 
 /* Parse, check, partition (fibers -> SLB processes, paper Sec. 5.1) and lower

@@ -108,6 +108,7 @@ typedef struct {
 
 typedef struct {
     const onet *net;
+    int n_mem;            /* copy of net->n_mem: freeing an instance never reads its net */
     uint64_t key;         /* stimulus key of this instance */
     uint64_t cycle;
     uint64_t *reg;        /* current register values */
@@ -605,6 +606,7 @@ osim *orc_sim_new(const onet *n, uint64_t seed, uint64_t inst)
 {
     osim *s = calloc(1, sizeof(osim));
     s->net = n;
+    s->n_mem = n->n_mem;
     s->reg = calloc((size_t)n->n_reg + 1, sizeof(uint64_t));
     s->reg_nx = calloc((size_t)n->n_reg + 1, sizeof(uint64_t));
     s->reg_start = calloc((size_t)n->n_reg + 1, sizeof(uint64_t));
@@ -621,7 +623,7 @@ osim *orc_sim_new(const onet *n, uint64_t seed, uint64_t inst)
 void orc_sim_free(osim *s)
 {
     if (!s) return;
-    for (int m = 0; m < s->net->n_mem; m++) free(s->mem[m]);
+    for (int m = 0; m < s->n_mem; m++) free(s->mem[m]);
     free(s->mem); free(s->reg); free(s->reg_nx); free(s->reg_start); free(s->val); free(s->in_val);
     free(s->in_hold); free(s->held);
     free(s);

@@ -246,7 +246,6 @@ void sim_config_default(sim_config* cfg) {
     cfg->struct_size = sizeof(sim_config);
     cfg->mode = SIM_MODE_AUTO;
     cfg->kernel = SIM_KERNEL_PERSISTENT;
-    cfg->chain = 2;
     cfg->timeout_ms = 2000;
     cfg->big_array_bytes = 128 * 1024;
 }

@@ -58,8 +58,8 @@ def mid_text():
 
 TINY_CASES = [
     (dict(mode="lane_op"), 1, [0]),
-    (dict(mode="lane_op", chain=0), 1, [0]),
-    (dict(mode="lane_op", chain=0, cluster_size=4, warps_per_cta=2, target_processes=16), 1, [0]),
+    (dict(mode="lane_op", chain=2), 1, [0]),
+    (dict(mode="lane_op", chain=2, cluster_size=4, warps_per_cta=2, target_processes=16), 1, [0]),
     (dict(mode="lane_op", lowering="generated"), 1, [0]),
     (dict(mode="lane_op", kernel="per_cycle"), 1, [0]),
     (dict(mode="lane_op", cluster_size=8, warps_per_cta=2, target_processes=16), 1, [0]),
@@ -80,18 +80,18 @@ def test_tiny_dumps(tiny_text, cfg, n_inst, insts):
     (dict(mode="lane_op", cluster_size=2, warps_per_cta=1, target_processes=2), 1, [0]),
     (dict(mode="lane_inst"), 33, [0, 32]),
     (dict(mode="lane_inst", lowering="generated"), 33, [0, 32]),
-    (dict(mode="lane_op", chain=0), 1, [0]),
-], ids=["lane_op", "lane_op_gen", "cluster", "lane_inst", "lane_inst_gen", "lane_op_unchained"])
+    (dict(mode="lane_op", chain=2), 1, [0]),
+], ids=["lane_op", "lane_op_gen", "cluster", "lane_inst", "lane_inst_gen", "lane_op_pairs"])
 def test_rom_ram_dumps(cfg, n_inst, insts):
     run_dumps(ROM_RAM, cfg, n_inst, insts, 7, 300)
 
 
 @pytest.mark.parametrize("cfg,n_inst,insts", [
     (dict(mode="lane_op"), 1, [0]),
-    (dict(mode="lane_op", chain=0), 1, [0]),
+    (dict(mode="lane_op", chain=2), 1, [0]),
     (dict(mode="lane_op", cluster_size=4, warps_per_cta=4), 1, [0]),
-    (dict(mode="lane_op", cluster_size=6, warps_per_cta=4, chain=0), 1, [0]),
+    (dict(mode="lane_op", cluster_size=6, warps_per_cta=4, chain=2), 1, [0]),
     (dict(mode="lane_inst", lowering="generated", kernel="persistent_graph"), 64, [0, 63]),
-], ids=["grid_barrier", "grid_barrier_unchained", "cluster4x4", "cluster6x4_unchained", "batched_generated"])
+], ids=["grid_barrier", "grid_barrier_pairs", "cluster4x4", "cluster6x4_pairs", "batched_generated"])
 def test_mid_dumps(mid_text, cfg, n_inst, insts):
     run_dumps(mid_text, cfg, n_inst, insts, 42, 1000)
