@@ -45,16 +45,16 @@ struct DIns {
 // such a step may hold up to kLeafStepMax instructions, four per lane.
 constexpr uint32_t kStepGeneric = 1u << 31;
 constexpr uint32_t kStepLeaf = 1u << 30;
-// A chain step (also kStepGeneric) holds the first operators of its n lanes,
-// then the second operators of its first m lanes (m - 1 in bits 24-28 of the
-// step word; count = n + m): lane i < m runs operator i, then operator n + i,
-// without a warp barrier between them.  A second operator's imm bits 0/1/2
-// mark operands a/b/c that are the lane's first result, taken from a register
-// (their slot fields name that result's slot, so the step also reads as two
-// sequential rows).
+// A chain step (also kStepGeneric) holds two rows (bits 24-27 of the step
+// word hold the row count) of n = count / 2 operators: lane i runs operator
+// i, then operator n + i, without a warp barrier between them (D_NOP in the
+// second row where a lane has one operator).  A second-row operator's imm
+// bits 0/1/2 mark operands a/b/c that are the lane's first result, taken
+// from a register (their slot fields name that result's slot, so the two
+// rows also read as sequential steps).
 constexpr uint32_t kStepChain = 1u << 29;
-constexpr uint32_t kStepPairsShift = 24;
-constexpr uint32_t kStepPairsMask = 0x1fu;
+constexpr uint32_t kStepRowsShift = 24;
+constexpr uint32_t kStepRowsMask = 0xfu;
 constexpr uint32_t kChainMax = 2;
 constexpr uint32_t kStepCountMask = 0xffu;
 constexpr uint32_t kLeafStepMax = 128;

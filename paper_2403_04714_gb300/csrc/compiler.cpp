@@ -1457,22 +1457,25 @@ int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words
 }
 
 
-// Compact program with operator chains (sim_config.chain = K = 2: pairs).  Operators are
+// Compact program with operator chains (sim_config.chain = K = 2; the
+// scheduler takes any K, the interpreter runs pairs).  Operators are
 // scheduled in dependence order; an operator whose operands are all ready
 // before the step of one of them, d, or come from d's lane in that step, runs
 // in d's step right after d on the same lane (up to K operators per lane),
 // taking d's result from a register instead of from the slot after a warp
-// barrier.  A step with pairs (kStepChain) holds its n lanes' first
-// operators, then the second operators of the m lanes that have one (those
-// lanes first); imm bits 0/1/2 mark operands a/b/c that are the previous
-// result of the lane.  Memory reads never
+// barrier.  A step with chains (kStepChain) holds R rows of its n lanes'
+// operators (D_NOP where a lane's chain is shorter); imm bits 0/1/2 mark
+// operands a/b/c that are the previous result of the lane.  Memory reads never
 // chain.  Slots are allocated over the compact steps (a value lives from its
 // step to the end of the step of its last use).
 // Measured on the mid netlist (one GB300, 4-CTA clusters): pairs take the
 // slowest process from 66 to 40 steps and the rate from 77-78k to 83-84k
 // cycles/s; chains of three or four (31 and 28 steps) gain nothing more,
 // because a step costs about as much to enter (instruction and operand loads,
-// store, warp barrier) as one more operator costs to evaluate.
+// store, warp barrier) as one more operator costs to evaluate.  A variant
+// that kept only the pairs' second operators (no D_NOP, lanes with a pair
+// first) made smaller programs but measured 4 % slower on the same GPU
+// (79.3k against 82.6k cycles/s), so the rows stay full.
 template <class MakeIns, class Operands>
 int chained_program(const Netlist& nl, const std::vector<Item>& items, const std::vector<int32_t>& local, size_t n_local,
                     MakeIns& make_ins, Operands& operands, Lowered& out, size_t p, uint32_t K, std::string& err) {
@@ -1537,16 +1540,12 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
         ps.push_back(std::move(st));
     }
     for (size_t s = 0; s < lanes.size(); s++) {
-        // lanes with a pair first, so the second row holds only the pairs
-        std::stable_sort(lanes[s].begin(), lanes[s].end(),
-                         [](const std::vector<int32_t>& x, const std::vector<int32_t>& y) { return x.size() > y.size(); });
-        uint32_t pairs = 0;
-        for (auto& L : lanes[s]) pairs += L.size() > 1;
-        PStep st{has_memrd[s] ? kStepGeneric
-                 : pairs ? (kStepGeneric | kStepChain | ((pairs - 1) << kStepPairsShift)) : 0u,
+        uint32_t rows = 1;
+        for (auto& L : lanes[s]) rows = std::max<uint32_t>(rows, uint32_t(L.size()));
+        PStep st{has_memrd[s] ? kStepGeneric : rows > 1 ? (kStepGeneric | kStepChain | (rows << kStepRowsShift)) : 0u,
                  {}, uint32_t(lanes[s].size())};
-        for (auto& L : lanes[s]) st.its.push_back(int64_t(opers[L[0]]));
-        for (uint32_t k = 0; k < pairs; k++) st.its.push_back(int64_t(opers[lanes[s][k][1]]));
+        for (uint32_t r = 0; r < rows; r++)
+            for (auto& L : lanes[s]) st.its.push_back(r < L.size() ? int64_t(opers[L[r]]) : -1);
         ps.push_back(std::move(st));
     }
     for (size_t k = 0; k < sinks.size(); k += 32) {
@@ -1576,6 +1575,12 @@ int chained_program(const Netlist& nl, const std::vector<Item>& items, const std
         const uint32_t n = ps[b].lanes;
         for (size_t j = 0; j < ps[b].its.size(); j++) {
             const int64_t i = ps[b].its[j];
+            if (i < 0) {
+                DIns nop{};                   // D_NOP (its result goes to the spare slot)
+                nop.w = 64;
+                st.ins.push_back(nop);
+                continue;
+            }
             DIns d = make_ins(items[size_t(i)], slot);
             if ((ps[b].flags & kStepChain) && j >= n) {
                 // operands that are the lane's previous result come from its register
@@ -1917,7 +1922,7 @@ std::vector<CStep> read_steps(const Lowered& low, size_t p) {
     std::vector<CStep> steps(nb);
     for (uint32_t b = 0; b < nb; b++) {
         const uint32_t e = w[1 + b], first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        steps[b].flags = e & (kStepGeneric | kStepLeaf | kStepChain | (kStepPairsMask << kStepPairsShift));
+        steps[b].flags = e & (kStepGeneric | kStepLeaf | kStepChain | (kStepRowsMask << kStepRowsShift));
         steps[b].ins.assign(ins + first, ins + first + cnt);
     }
     return steps;
@@ -2162,8 +2167,8 @@ int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_
         low.s_off[p] = uint32_t(low.s_ins.size() / 32);
         for (const auto& st : steps[p]) {
             // a chain step reads as two rows: the first operators, then the second ones
-            const size_t pairs = (st.flags & kStepChain) ? ((st.flags >> kStepPairsShift) & kStepPairsMask) + 1 : 0;
-            const size_t row = pairs ? st.ins.size() - pairs : 32;
+            const size_t row = (st.flags & kStepChain) ? st.ins.size() / ((st.flags >> kStepRowsShift) & kStepRowsMask)
+                                                       : 32;
             for (size_t k = 0; k < std::max<size_t>(1, st.ins.size()); k += row) {
                 const size_t base = low.s_ins.size();
                 low.s_ins.resize(base + 32, DIns{});

@@ -390,20 +390,20 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
             const Dec d = decode(ins[on ? first + lane : first]);
             sl[on ? d.dst : dummy] = eval_op(d, sl[d.a], sl[d.b], sl[d.c]);
         } else if (e & kStepChain) {
-            // each lane's first operator, then, for the first m lanes, a second
-            // one (no warp barrier between them); imm bits 0/1/2 take operands
-            // a/b/c of the second from the first result.  Other lanes repeat
-            // the first second operator into the spare slot.
-            const uint32_t m = ((e >> kStepPairsShift) & kStepPairsMask) + 1, n = cnt - m;
-            const bool on = lane < n, on2 = lane < m;
-            const Dec d1 = decode(ins[on ? first + lane : first]);
-            const Dec d2 = decode(ins[first + n + (on2 ? lane : 0)]);
+            // two rows: each lane's first operator, then its second one (no
+            // warp barrier between them); imm bits 0/1/2 take operands a/b/c
+            // of the second from the first result
+            const uint32_t n = cnt >> 1;
+            const bool on = lane < n;
+            const uint32_t i1 = on ? first + lane : first;
+            const Dec d1 = decode(ins[i1]);
+            const Dec d2 = decode(ins[i1 + n]);
             const uint64_t r1 = eval_op(d1, sl[d1.a], sl[d1.b], sl[d1.c]);
             sl[on ? d1.dst : dummy] = r1;
             const uint64_t a2 = (d2.imm & 1u) ? r1 : sl[d2.a];
             const uint64_t b2 = (d2.imm & 2u) ? r1 : sl[d2.b];
             const uint64_t c2 = (d2.imm & 4u) ? r1 : sl[d2.c];
-            sl[on2 ? d2.dst : dummy] = eval_op(d2, a2, b2, c2);
+            sl[on && d2.op != D_NOP ? d2.dst : dummy] = eval_op(d2, a2, b2, c2);
         } else if (e & kStepLeaf) {
             // up to four leaves per lane, every load in flight before the
             // first value is stored; idle lanes write the spare slot

@@ -55,13 +55,13 @@ class Emu:
                 for e in table:
                     first, cnt = int(e) & 0xffff, (int(e) >> 16) & 0xff
                     chain = (int(e) >> 29) & 1
-                    pairs = ((int(e) >> 24) & 0x1F) + 1 if chain else 0
-                    assert cnt <= 32 or (int(e) >> 30) & 1 or (chain and cnt - pairs <= 32), \
+                    n_rows_step = (int(e) >> 24) & 0xF if chain else 1
+                    assert cnt <= 32 or (int(e) >> 30) & 1 or (chain and cnt <= 32 * n_rows_step), \
                         "only leaf and chain steps may exceed 32 lanes"
-                    # a chain step holds the lanes' first operators, then the
-                    # second operators of its first lanes (reading the first
-                    # result's slot): two sequential rows
-                    width = cnt - pairs if chain else 32
+                    # a chain step holds rows of the lanes' operators, each
+                    # lane's next operator in the next row (reading the
+                    # previous result's slot): as many sequential rows
+                    width = cnt // n_rows_step if chain else 32
                     for k in range(0, max(cnt, 1), width):
                         row = np.zeros(32, dtype=DINS)
                         n = min(width, cnt - k)

@@ -36,34 +36,42 @@ def writes(d):
 
 
 def check_chain_step(p, b, e, step, valid, slots):
-    """A chain step: n first operators, then the second operators of lanes
-    0..m-1 (m - 1 in bits 24-28).  An operand flagged in imm bits 0/1/2 names
-    the slot of the lane's first operator; every other operand was written by
-    an earlier step; no slot is written twice, and no slot written in the
-    step is read there except through the flag."""
-    m = ((e >> 24) & 0x1F) + 1
-    n = len(step) - m
-    assert e & GENERIC and 1 <= m <= n <= 32, (p, b)
-    firsts, seconds = step[:n], step[n:]
-    assert all(int(d["op"]) in ALU for d in step), (p, b)
-    dsts = [int(d["dst"]) for d in step]
+    """A chain step: R rows (bits 24-27) of n operators; lane i runs the
+    operators i, n + i, ... in order (D_NOP after the end of its chain).  An
+    operand flagged in imm bits 0/1/2 names the slot of the lane's previous
+    operator; every other operand was written by an earlier step or earlier
+    in the lane's own chain; no slot is written twice, and no slot written in
+    the step is read there by another lane."""
+    rows = (e >> 24) & 0xF
+    assert e & GENERIC and rows >= 2 and len(step) % rows == 0 and len(step) // rows <= 32, (p, b)
+    n = len(step) // rows
+    grid = [step[r * n:(r + 1) * n] for r in range(rows)]
+    assert all(int(d["op"]) in ALU for d in grid[0]), (p, b)
+    dsts = [int(d["dst"]) for row in grid for d in row if int(d["op"]) != 0]
     assert len(dsts) == len(set(dsts)), (p, b, "slot written twice in one step")
-    reads = set()
-    for d in firsts:
-        for s in _reads(d):
-            assert s in valid, (p, b, "operand slot read before any write")
-            reads.add(s)
-    for f, d in zip(firsts, seconds):
-        flags = int(d["imm"])
-        names = ["a", "b", "c"][:len(_reads(d))]
-        assert flags and not flags >> len(names), (p, b, "a second operator must use its lane's first result")
-        for k, name in enumerate(names):
-            if flags >> k & 1:
-                assert int(d[name]) == int(f["dst"]), (p, b, "chained operand names the first result's slot")
-            else:
-                assert int(d[name]) in valid, (p, b, "operand slot read before any write")
-                reads.add(int(d[name]))
-    assert not reads & set(dsts), (p, b, "slot read and written in one step")
+    chained = 0
+    for lane in range(n):
+        own = set()                     # slots this lane wrote earlier in the step
+        ended = False
+        for r in range(rows):
+            d = grid[r][lane]
+            if int(d["op"]) == 0:
+                ended = True
+                continue
+            assert int(d["op"]) in ALU and not ended, (p, b, "chains are contiguous operator runs")
+            flags = int(d["imm"]) if r else 0
+            names = ["a", "b", "c"][:len(_reads(d))]
+            assert not flags >> len(names), (p, b)
+            for k, name in enumerate(names):
+                sl = int(d[name])
+                if flags >> k & 1:
+                    assert sl == int(grid[r - 1][lane]["dst"]), (p, b, "chained operand names the previous result")
+                    chained += 1
+                else:
+                    assert sl in valid or sl in own, (p, b, "operand slot read before any write")
+                    assert sl in own or sl not in dsts, (p, b, "slot written in this step read by another lane")
+            own.add(int(d["dst"]))
+    assert chained > 0
     for s in dsts:
         assert s < int(slots[p])
         valid[s] = b
