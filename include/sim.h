@@ -339,7 +339,11 @@ typedef struct sim_server_config {
     uint32_t pool_slots;        /* instance slots per pool (default 1024) */
     uint64_t hbm_cap_bytes;     /* device-memory cap for all pools (default 150 GiB) */
     uint32_t chunk_cycles;      /* cycles per pool step (default 1000) */
-    uint32_t reserved[7];
+    uint32_t persistent;        /* 1 (default): a pool step is one persistent launch that runs all its jobs'
+                                 * instance groups across the step's cycles (grid barrier between cycles, grid
+                                 * sized to the groups in use, so pools of other netlists still share the GPU);
+                                 * 0: one launch per cycle, replayed from a CUDA graph */
+    uint32_t reserved[6];
 } sim_server_config;
 
 typedef struct sim_job {

@@ -14,12 +14,15 @@ struct sim_netlist;
 struct sim_batch;
 
 namespace rtl {
-int pool_create(sim_netlist* nl, uint32_t capacity, sim_batch** out);
+// persistent: each pool_step is one persistent launch (grid barrier between
+// cycles, grid sized to the active instance groups); else per-cycle graphs.
+int pool_create(sim_netlist* nl, uint32_t capacity, bool persistent, sim_batch** out);
 // Give slots [lo, lo+n) to a job: stimulus keys of instances 0..n-1 of `seed`,
 // cycle origin = the pool's current cycle, state reset to the initial state.
 int pool_admit(sim_batch* b, uint32_t lo, uint32_t n, uint64_t seed);
-// Enqueue `n` cycles for the active slots (asynchronous on the pool's stream).
-int pool_step(sim_batch* b, uint64_t n);
+// Enqueue `n` cycles for the active slots (asynchronous on the pool's stream);
+// *kernels receives the number of kernels it launched.
+int pool_step(sim_batch* b, uint64_t n, uint64_t* kernels);
 // Simulate only instance groups [0, n_groups) (32 slots each) from the next
 // step on: slots are taken first-fit, so the occupied ones sit at the front.
 int pool_set_active(sim_batch* b, uint32_t n_groups);

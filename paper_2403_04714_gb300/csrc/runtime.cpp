@@ -1548,14 +1548,15 @@ size_t pool_footprint(const sim_netlist* h, uint32_t capacity) {
     return size_t(per * I + prog + 2 * h->mem_word_off.back() * 8);
 }
 
-int pool_create(sim_netlist* nl, uint32_t capacity, sim_batch** out) {
+int pool_create(sim_netlist* nl, uint32_t capacity, bool persistent, sim_batch** out) {
     if (!nl || !out || capacity == 0) return set_err(SIM_ERR_BADARG, "bad argument");
-    // a pool runs lane = instance with per-cycle graphs and no digest ring,
-    // whatever the netlist was loaded for (its LANE_INST program is always
-    // there, also when the LANE_OP program was lowered for clusters)
+    // a pool runs lane = instance with no digest ring, whatever the netlist
+    // was loaded for (its LANE_INST program is always there, also when the
+    // LANE_OP program was lowered for clusters): one persistent launch per
+    // step, or per-cycle launches replayed from a graph
     sim_config cfg = nl->cfg;
     cfg.mode = SIM_MODE_LANE_INST;
-    cfg.kernel = SIM_KERNEL_PER_CYCLE_GRAPH;
+    cfg.kernel = persistent ? SIM_KERNEL_PERSISTENT : SIM_KERNEL_PER_CYCLE_GRAPH;
     cfg.digest_capacity = 0;
     cfg.cluster_size = 0;
     int rc = create_instances(nl, cfg, capacity, 0, nullptr, out);
@@ -1601,12 +1602,20 @@ int pool_admit(sim_batch* b, uint32_t lo, uint32_t n, uint64_t seed) {
     return SIM_OK;
 }
 
-int pool_step(sim_batch* b, uint64_t n) { return sim_step(b, n); }
+int pool_step(sim_batch* b, uint64_t n, uint64_t* kernels) {
+    const uint64_t k0 = b->kernels_launched;
+    int rc = sim_step(b, n);
+    *kernels = b->kernels_launched - k0;
+    return rc;
+}
 
 int pool_set_active(sim_batch* b, uint32_t n_groups) {
     if (!b || !b->pool || b->mode != SIM_MODE_LANE_INST || n_groups == 0 || uint64_t(n_groups) * 32 > b->I)
         return set_err(SIM_ERR_BADARG, "bad active group count");
     b->n_tasks = uint32_t(b->nl->part.procs.size()) * n_groups;
+    // a persistent step holds only the CTAs its tasks need, leaving the other
+    // SMs to the pools of other netlists
+    b->grid = std::max(1, std::min(int((b->n_tasks + b->warps - 1) / b->warps), b->max_grid));
     return SIM_OK;
 }
 

@@ -4,8 +4,10 @@
 // server thread keeps one instance pool per netlist on the device (pool.hpp);
 // a job is admitted when its pool has a free run of slots, creating the pool
 // if the device-memory footprint of all pools stays under the cap.  Every
-// pool is stepped on its own stream with launch-per-cycle kernels, so pools
-// of different netlists run concurrently on the GPU, and each step advances
+// pool is stepped on its own stream, by one persistent launch per step whose
+// grid covers only the pool's instance groups in use (or, as configured, by
+// per-cycle launches replayed from a graph), so pools of different netlists
+// run concurrently on the GPU, and each step advances
 // every job in the pool by the same number of cycles (never past the
 // earliest-finishing job's budget).  A finished job's digests are read, its
 // slots freed, and queued jobs take them at the next step boundary.
@@ -133,7 +135,7 @@ bool sim_server::try_admit(Job& j) {
         p->capacity = cap;
         p->bytes = bytes;
         p->slot_job.assign(cap, 0);
-        int rc = rtl::pool_create(j.spec.netlist, cap, &p->batch);
+        int rc = rtl::pool_create(j.spec.netlist, cap, cfg.persistent != 0, &p->batch);
         if (rc) {
             j.state = SIM_JOB_FAILED;
             j.error = sim_last_error();
@@ -259,8 +261,9 @@ void sim_server::run() {
                         hi = std::max(hi, jobs[id]->slot_lo + jobs[id]->spec.n_inst);
                     }
                 }
+                uint64_t launched = 0;
                 int rc = rtl::pool_set_active(p.batch, (hi + 31) / 32);
-                if (!rc) rc = rtl::pool_step(p.batch, n);
+                if (!rc) rc = rtl::pool_step(p.batch, n, &launched);
                 if (!rc && cudaEventRecord(p.done_ev, rtl::pool_stream(p.batch)) != cudaSuccess) rc = SIM_ERR_CUDA;
                 if (rc) {
                     fail_pool_jobs(p, sim_last_error());
@@ -268,7 +271,7 @@ void sim_server::run() {
                 }
                 p.step_n = n;
                 p.inflight = true;
-                kernels += n + 1;
+                kernels += launched;
             }
             any_inflight |= p.inflight;
         }
@@ -316,6 +319,7 @@ void sim_server_config_default(sim_server_config* c) {
     c->hbm_cap_bytes = 150ULL << 30;
     c->pool_slots = 1024;
     c->chunk_cycles = 1000;
+    c->persistent = 1;
 }
 
 int sim_server_create(const sim_server_config* cfg, sim_server** out) {

@@ -116,7 +116,7 @@ JOB_STATES = {0: "queued", 1: "running", 2: "done", 3: "failed"}
 
 class sim_server_config(C.Structure):
     _fields_ = [("struct_size", C.c_uint32), ("pool_slots", C.c_uint32), ("hbm_cap_bytes", C.c_uint64),
-                ("chunk_cycles", C.c_uint32), ("reserved", C.c_uint32 * 7)]
+                ("chunk_cycles", C.c_uint32), ("persistent", C.c_uint32), ("reserved", C.c_uint32 * 6)]
 
 
 class sim_job(C.Structure):

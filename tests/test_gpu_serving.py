@@ -33,9 +33,10 @@ def nets():
     return {"tiny": tiny, "flat": flat}
 
 
-def test_jobs_alone_and_in_the_mix(nets):
+@pytest.mark.parametrize("persistent", [1, 0], ids=["persistent_pools", "per_cycle_pools"])
+def test_jobs_alone_and_in_the_mix(nets, persistent):
     handles = {k: sim.Netlist(v) for k, v in nets.items()}
-    srv = sim.Server(pool_slots=256, chunk_cycles=97)
+    srv = sim.Server(pool_slots=256, chunk_cycles=97, persistent=persistent)
     # (netlist, instances, seed, cycles, submit delay): arrivals overlap running jobs
     jobs = [("tiny", 1, 5, 1000, 0.0), ("flat", 40, 6, 700, 0.0), ("tiny", 33, 7, 2500, 0.01),
             ("tiny", 3, 8, 300, 0.02), ("flat", 1, 9, 1234, 0.03), ("tiny", 100, 10, 600, 0.05),
@@ -91,4 +92,29 @@ def test_pool_of_a_cluster_lowered_netlist(nets):
     srv.wait(jid)
     assert srv.poll(jid)["state"] == "done"
     assert np.array_equal(srv.digests(jid, 40), solo(nets["tiny"], 40, 21, 300))
+    srv.close()
+
+
+def test_job_admitted_while_a_persistent_step_runs(nets):
+    # a long job keeps its pool stepping (one persistent launch per 2,000
+    # cycles); jobs of the same netlist that arrive meanwhile join the pool at
+    # the next step boundary and overlap the long one, and every result equals
+    # the same job run alone
+    nl = sim.Netlist(nets["tiny"])
+    srv = sim.Server(pool_slots=256, chunk_cycles=2000, persistent=1)
+    long_id = srv.submit(nl, 64, 31, 60_000)
+    t0 = time.time()
+    while srv.poll(long_id)["cycles_done"] < 2000 and time.time() - t0 < 60:
+        time.sleep(0.001)
+    late = [srv.submit(nl, 5, 32, 3000), srv.submit(nl, 40, 33, 1500)]
+    for jid in late:
+        srv.wait(jid)
+    assert srv.poll(long_id)["state"] == "running"          # the late jobs finished inside the long one
+    srv.wait(long_id)
+    st_long = srv.poll(long_id)
+    for jid, (n, seed, cyc) in zip(late, ((5, 32, 3000), (40, 33, 1500))):
+        st = srv.poll(jid)
+        assert st["state"] == "done" and st_long["t_start"] < st["t_start"] < st["t_done"] < st_long["t_done"]
+        assert np.array_equal(srv.digests(jid, n), solo(nets["tiny"], n, seed, cyc))
+    assert np.array_equal(srv.digests(long_id, 64), solo(nets["tiny"], 64, 31, 60_000))
     srv.close()
