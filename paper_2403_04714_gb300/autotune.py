@@ -1,9 +1,10 @@
 """Autotuner for the launch configuration of a netlist on this GPU.
 
 Candidates vary what the compiler cannot decide alone: the partition size
-(SLB target process count), warps per CTA (with lane = instance: instances
-per CTA = 32 x warps), the task order, the lowering and, for one instance,
-the thread-block cluster size of the distributed-shared-memory exchange.  Each candidate is
+(SLB target process count), the partitioning strategy, warps per CTA (with
+lane = instance: instances per CTA = 32 x warps), the task order, the
+lowering, operator pairs and, for one instance, the thread-block cluster size
+of the distributed-shared-memory exchange.  Each candidate is
 timed on a short run of the real workload with CUDA events; the best one is
 persisted in a JSON cache keyed by a hash of the netlist text, the instance
 count, the GPU name and the built library, so later runs with the same
@@ -53,6 +54,10 @@ def default_candidates(n_inst: int, sms: int = 152):
     if n_inst == 1:     # cluster exchange (one instance): several clusters, and one 16-CTA cluster
         cands += [dict(mode="lane_op", lowering="bytecode", chain=2, cluster_size=c, warps_per_cta=w)
                   for c, w in ((4, 4), (6, 4), (2, 4), (16, 8))]
+        # the hypergraph partitioning strategy (Sec. 7) on the two cluster shapes
+        # that measured best with the bottom-up merge
+        cands += [dict(mode="lane_op", lowering="bytecode", chain=2, cluster_size=c, warps_per_cta=4,
+                       partitioner="hypergraph") for c in (2, 4)]
     return cands
 
 

@@ -25,7 +25,9 @@ int pool_admit(sim_batch* b, uint32_t lo, uint32_t n, uint64_t seed);
 int pool_step(sim_batch* b, uint64_t n, uint64_t* kernels);
 // Simulate only instance groups [0, n_groups) (32 slots each) from the next
 // step on: slots are taken first-fit, so the occupied ones sit at the front.
-int pool_set_active(sim_batch* b, uint32_t n_groups);
+// A persistent step then launches at most max_grid / share CTAs, so that
+// `share` pools stepping at once fit on the GPU side by side.
+int pool_set_active(sim_batch* b, uint32_t n_groups, uint32_t share);
 // State digests of slots [lo, lo+n) (synchronises the pool's stream).
 int pool_digests(sim_batch* b, uint32_t lo, uint32_t n, uint64_t* out);
 // Device bytes a pool of `capacity` slots of this netlist holds.

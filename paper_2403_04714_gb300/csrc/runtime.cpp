@@ -1609,13 +1609,14 @@ int pool_step(sim_batch* b, uint64_t n, uint64_t* kernels) {
     return rc;
 }
 
-int pool_set_active(sim_batch* b, uint32_t n_groups) {
+int pool_set_active(sim_batch* b, uint32_t n_groups, uint32_t share) {
     if (!b || !b->pool || b->mode != SIM_MODE_LANE_INST || n_groups == 0 || uint64_t(n_groups) * 32 > b->I)
         return set_err(SIM_ERR_BADARG, "bad active group count");
     b->n_tasks = uint32_t(b->nl->part.procs.size()) * n_groups;
-    // a persistent step holds only the CTAs its tasks need, leaving the other
-    // SMs to the pools of other netlists
-    b->grid = std::max(1, std::min(int((b->n_tasks + b->warps - 1) / b->warps), b->max_grid));
+    // a persistent step holds only the CTAs its tasks need, and at most its
+    // share of the GPU, leaving the other SMs to the pools of other netlists
+    const int cap = std::max(1, b->max_grid / int(std::max(1u, share)));
+    b->grid = std::max(1, std::min(int((b->n_tasks + b->warps - 1) / b->warps), cap));
     return SIM_OK;
 }
 

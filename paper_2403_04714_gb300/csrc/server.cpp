@@ -247,8 +247,11 @@ void sim_server::run() {
             }
             queue.swap(waiting);
         }
-        // start a step on every idle pool with jobs
+        // start a step on every idle pool with jobs; persistent steps of the
+        // pools with jobs split the GPU between them
         bool any_inflight = false;
+        uint32_t busy = 0;
+        for (auto& pp : pools) busy += !pp->active.empty();
         for (auto& pp : pools) {
             Pool& p = *pp;
             if (!p.inflight && !p.active.empty()) {
@@ -262,7 +265,7 @@ void sim_server::run() {
                     }
                 }
                 uint64_t launched = 0;
-                int rc = rtl::pool_set_active(p.batch, (hi + 31) / 32);
+                int rc = rtl::pool_set_active(p.batch, (hi + 31) / 32, busy);
                 if (!rc) rc = rtl::pool_step(p.batch, n, &launched);
                 if (!rc && cudaEventRecord(p.done_ev, rtl::pool_stream(p.batch)) != cudaSuccess) rc = SIM_ERR_CUDA;
                 if (rc) {
