@@ -168,7 +168,10 @@ void sim_netlist_destroy(sim_netlist *nl);
 
 /* Generate and compile (NVRTC + nvJitLink, no GPU needed) the generated-CUDA
  * lowering of one lane mapping ahead of sim_create_instances, e.g. to fill
- * the $RTLSIM_GENCACHE cache.  *seconds: compile (or cache read) time;
+ * the $RTLSIM_GENCACHE cache.  This compiles the module without per-cycle
+ * digest code (batches with digest_capacity = 0); a batch that keeps digests
+ * compiles its own module, whose process functions add the digest terms, at
+ * its sim_create_instances.  *seconds: compile (or cache read) time;
  * *cached: 1 if the linked module came from the cache.  Errors: BADARG, CUDA
  * (compile or link failure, message in sim_last_error). */
 int sim_netlist_compile_generated(sim_netlist *nl, int32_t mode, double *seconds, int32_t *cached);

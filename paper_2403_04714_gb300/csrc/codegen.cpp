@@ -48,6 +48,7 @@ struct Emitter {
     const Netlist& nl;
     const RegLayout& L;
     int mode;
+    bool digest;                  // emit the per-cycle digest terms
     std::string& o;
     std::vector<int32_t> local;   // node -> local index (-1 = not in this process)
     std::vector<uint8_t> done;
@@ -159,7 +160,9 @@ struct Emitter {
         } else {
             o += "      n1[" + std::to_string(ix) + "ull * BS + inst] = (uint32_t)sv;\n";
         }
-        o += "      if (col >= 0) *dacc += mix64((" + hex64(uint64_t(r) * 0x9E3779B97F4A7C15ULL + 1ULL) + ") ^ sv); }\n";
+        if (digest)
+            o += "      if (col >= 0) *dacc += mix64((" + hex64(uint64_t(r) * 0x9E3779B97F4A7C15ULL + 1ULL) + ") ^ sv);\n";
+        o += "    }\n";
     }
 
     void wrec(int32_t port) {
@@ -171,6 +174,10 @@ struct Emitter {
     }
 
     void commit(int32_t m) {
+        if (!digest) {
+            o += "    if (pending) mem_commit(P, S, " + std::to_string(m) + "u, inst, nxt, false);\n";
+            return;
+        }
         o += "    if (pending) { const uint64_t dl = mem_commit(P, S, " + std::to_string(m) +
              "u, inst, nxt, S.ring_cap != 0 && col >= 0);\n"
              "      if (S.ring_cap) mem_digest_update(S, " + std::to_string(m) + "u, inst, t, dl); }\n";
@@ -242,12 +249,13 @@ std::vector<int32_t> fiber_order(const Partition& part, size_t p, const std::vec
 
 }  // namespace
 
-void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p, int mode, std::string& o) {
+void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p, int mode, bool digest,
+                 std::string& o) {
     std::vector<int32_t> nodes;
     for (int32_t f : part.procs[p]) nodes.insert(nodes.end(), part.fibers[f].nodes.begin(), part.fibers[f].nodes.end());
     std::sort(nodes.begin(), nodes.end());
     nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
-    Emitter E{nl, L, mode, o, std::vector<int32_t>(nl.nodes.size(), -1), std::vector<uint8_t>(nodes.size(), 0)};
+    Emitter E{nl, L, mode, digest, o, std::vector<int32_t>(nl.nodes.size(), -1), std::vector<uint8_t>(nodes.size(), 0)};
     bool has_input = false;
     for (size_t i = 0; i < nodes.size(); i++) {
         E.local[nodes[i]] = int32_t(i);
@@ -286,7 +294,7 @@ void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, s
     o += "}\n\n";
 }
 
-int gen_cuda(const Netlist& nl, const Partition& part, int mode, int n_chunks, std::vector<GenUnit>& out,
+int gen_cuda(const Netlist& nl, const Partition& part, int mode, bool digest, int n_chunks, std::vector<GenUnit>& out,
              std::string& err) {
     (void)err;
     const RegLayout L = reg_layout(nl);
@@ -310,7 +318,7 @@ int gen_cuda(const Netlist& nl, const Partition& part, int mode, int n_chunks, s
         uint64_t goal = total * uint64_t(c + 1) / uint64_t(n_chunks), acc = 0;
         for (size_t q = 0; q < p; q++) acc += weight[q];
         do {
-            gen_process(nl, part, L, p, mode, u.source);
+            gen_process(nl, part, L, p, mode, digest, u.source);
             acc += weight[p];
             p++;
         } while (p < NP && (acc < goal || c == n_chunks - 1));
@@ -326,7 +334,8 @@ int gen_cuda(const Netlist& nl, const Partition& part, int mode, int n_chunks, s
                 "uint64_t* __restrict__ dacc, int32_t col) {\n    switch (p) {\n";
     for (size_t q = 0; q < NP; q++)
         k.source += "    case " + std::to_string(q) + ": rtl_p" + std::to_string(q) + "(P, S, g, t, pending, lane, dacc, col); return;\n";
-    k.source += "    default: return;\n    }\n}\n\nRTLSIM_GEN_KERNELS(" + std::to_string(mode) + ")\n";
+    k.source += "    default: return;\n    }\n}\n\nRTLSIM_GEN_KERNEL(" + std::to_string(mode) + ", " +
+                (digest ? "true" : "false") + ")\n";
     out.push_back(std::move(k));
     return SIM_OK;
 }

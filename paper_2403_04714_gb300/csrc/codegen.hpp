@@ -14,15 +14,18 @@ struct GenUnit {
 };
 
 // CUDA sources for every process (in n_chunks units) plus the dispatcher and
-// the kernels rtl_gen_d0 / rtl_gen_d1 (digests off / on) for lane mapping `mode`.
-int gen_cuda(const Netlist& nl, const Partition& part, int mode, int n_chunks, std::vector<GenUnit>& out,
+// one kernel for lane mapping `mode`: rtl_gen_d1 with the per-cycle digest
+// code in every process function, or rtl_gen_d0 without any (its process
+// functions are that much shorter, which the instruction caches feel).
+int gen_cuda(const Netlist& nl, const Partition& part, int mode, bool digest, int n_chunks, std::vector<GenUnit>& out,
              std::string& err);
-void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p, int mode, std::string& o);
+void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p, int mode, bool digest,
+                 std::string& o);
 
 // A loaded generated module.
 struct GenModule {
     cudaLibrary_t lib = nullptr;
-    cudaKernel_t kernel[2] = {nullptr, nullptr};   // [digest]
+    cudaKernel_t kernel = nullptr;                 // rtl_gen_d0 or rtl_gen_d1
     double compile_seconds = 0;
     bool cached = false;
 };
@@ -32,8 +35,8 @@ struct GenModule {
 // `cache_dir` (empty: no cache) by a hash of the sources and options.
 int jit_compile(const std::vector<GenUnit>& units, const std::string& cache_dir, std::vector<char>& linked,
                 bool* cached, double* seconds, std::string& err);
-// Load a linked cubin on the current device and look up its kernels.
-int jit_load(const std::vector<char>& linked, GenModule& out, std::string& err);
+// Load a linked cubin on the current device and look up its kernel.
+int jit_load(const std::vector<char>& linked, bool digest, GenModule& out, std::string& err);
 void jit_unload(GenModule& m);
 
 }  // namespace rtl

@@ -177,21 +177,18 @@ int jit_compile(const std::vector<GenUnit>& units, const std::string& cache_dir,
     return SIM_OK;
 }
 
-int jit_load(const std::vector<char>& linked, GenModule& out, std::string& err) {
+int jit_load(const std::vector<char>& linked, bool digest, GenModule& out, std::string& err) {
     cudaError_t e = cudaLibraryLoadData(&out.lib, linked.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
     if (e != cudaSuccess) {
         err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
         return SIM_ERR_CUDA;
     }
-    const char* names[2] = {"rtl_gen_d0", "rtl_gen_d1"};
-    for (int d = 0; d < 2; d++) {
-        e = cudaLibraryGetKernel(&out.kernel[d], out.lib, names[d]);
-        if (e != cudaSuccess) {
-            err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
-            cudaLibraryUnload(out.lib);
-            out.lib = nullptr;
-            return SIM_ERR_CUDA;
-        }
+    e = cudaLibraryGetKernel(&out.kernel, out.lib, digest ? "rtl_gen_d1" : "rtl_gen_d0");
+    if (e != cudaSuccess) {
+        err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
+        cudaLibraryUnload(out.lib);
+        out.lib = nullptr;
+        return SIM_ERR_CUDA;
     }
     return SIM_OK;
 }
@@ -199,7 +196,7 @@ int jit_load(const std::vector<char>& linked, GenModule& out, std::string& err) 
 void jit_unload(GenModule& m) {
     if (m.lib) cudaLibraryUnload(m.lib);
     m.lib = nullptr;
-    m.kernel[0] = m.kernel[1] = nullptr;
+    m.kernel = nullptr;
 }
 
 }  // namespace rtl

@@ -136,12 +136,14 @@ struct sim_netlist {
     sim_config cfg;
     // generated-CUDA lowering, per lane mapping (built on first use)
     std::mutex gen_mu;
-    std::vector<char> gen_cubin[3];
-    rtl::GenModule gen[3];
-    double gen_seconds[3] = {0, 0, 0};
-    bool gen_cached[3] = {false, false, false};
+    // [lane mapping][digest]: the process functions with or without digest code
+    std::vector<char> gen_cubin[3][2];
+    rtl::GenModule gen[3][2];
+    double gen_seconds[3][2] = {};
+    bool gen_cached[3][2] = {};
     ~sim_netlist() {
-        for (auto& g : gen) rtl::jit_unload(g);
+        for (auto& gm : gen)
+            for (auto& g : gm) rtl::jit_unload(g);
     }
     Netlist nl;
     Partition part;
@@ -231,7 +233,7 @@ struct sim_batch {
 };
 
 namespace {
-int ensure_compiled(sim_netlist* h, int mode);
+int ensure_compiled(sim_netlist* h, int mode, bool digest);
 int create_instances(sim_netlist* nl, const sim_config& cfg, uint32_t n_inst, uint64_t seed, void* cuda_stream,
                      sim_batch** out);
 }
@@ -352,10 +354,10 @@ void sim_netlist_destroy(sim_netlist* nl) { delete nl; }
 
 int sim_netlist_compile_generated(sim_netlist* nl, int32_t mode, double* seconds, int32_t* cached) {
     if (!nl || (mode != SIM_MODE_LANE_OP && mode != SIM_MODE_LANE_INST)) return set_err(SIM_ERR_BADARG, "bad argument");
-    int rc = ensure_compiled(nl, mode);
+    int rc = ensure_compiled(nl, mode, false);
     if (rc) return rc;
-    if (seconds) *seconds = nl->gen_seconds[mode];
-    if (cached) *cached = nl->gen_cached[mode] ? 1 : 0;
+    if (seconds) *seconds = nl->gen_seconds[mode][0];
+    if (cached) *cached = nl->gen_cached[mode][0] ? 1 : 0;
     return SIM_OK;
 }
 
@@ -422,14 +424,14 @@ int sim_netlist_table(const sim_netlist* nl, int32_t which, void* out, size_t* b
 namespace {
 
 // Generate and compile (once per lane mapping) the netlist's CUDA lowering.
-int ensure_compiled(sim_netlist* h, int mode) {
+int ensure_compiled(sim_netlist* h, int mode, bool digest) {
     std::lock_guard<std::mutex> g(h->gen_mu);
-    if (!h->gen_cubin[mode].empty()) return SIM_OK;
+    if (!h->gen_cubin[mode][digest].empty()) return SIM_OK;
     std::vector<rtl::GenUnit> units;
     std::string err;
     unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     int chunks = int(std::min<size_t>(std::max<size_t>(1, h->part.procs.size() / 16), size_t(hw) * 2));
-    int rc = rtl::gen_cuda(h->nl, h->part, mode, chunks, units, err);
+    int rc = rtl::gen_cuda(h->nl, h->part, mode, digest, chunks, units, err);
     if (rc) return set_err(rc, err);
     if (const char* dump = getenv("RTLSIM_GEN_DUMP")) {     // developer aid: keep the generated sources
         for (auto& u : units) {
@@ -448,20 +450,20 @@ int ensure_compiled(sim_netlist* h, int mode) {
     }
     bool cached = false;
     double sec = 0;
-    rc = rtl::jit_compile(units, cache, h->gen_cubin[mode], &cached, &sec, err);
+    rc = rtl::jit_compile(units, cache, h->gen_cubin[mode][digest], &cached, &sec, err);
     if (rc) return set_err(rc, err);
-    h->gen_seconds[mode] = sec;
-    h->gen_cached[mode] = cached;
+    h->gen_seconds[mode][digest] = sec;
+    h->gen_cached[mode][digest] = cached;
     return SIM_OK;
 }
 
-int ensure_loaded(sim_netlist* h, int mode) {
-    int rc = ensure_compiled(h, mode);
+int ensure_loaded(sim_netlist* h, int mode, bool digest) {
+    int rc = ensure_compiled(h, mode, digest);
     if (rc) return rc;
     std::lock_guard<std::mutex> g(h->gen_mu);
-    if (h->gen[mode].lib) return SIM_OK;
+    if (h->gen[mode][digest].lib) return SIM_OK;
     std::string err;
-    rc = rtl::jit_load(h->gen_cubin[mode], h->gen[mode], err);
+    rc = rtl::jit_load(h->gen_cubin[mode][digest], digest, h->gen[mode][digest], err);
     if (rc) return set_err(rc, err);
     return SIM_OK;
 }
@@ -479,10 +481,7 @@ int plan_launch_gen(sim_batch* b) {
     b->warps = warps;
     b->threads = warps * 32;
     int occ = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->gen_kernel[0], b->threads, 0));
-    int occ1 = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, b->gen_kernel[1], b->threads, 0));
-    occ = std::min(occ, occ1);
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->gen_kernel[b->S.ring_cap > 0], b->threads, 0));
     if (occ < 1) return set_err(SIM_ERR_CAPACITY, "generated kernel does not fit on an SM");
     b->max_grid = occ * sms;
     int need = int((b->n_tasks + warps - 1) / warps);
@@ -1088,10 +1087,12 @@ int create_instances(sim_netlist* nl, const sim_config& cfg, uint32_t n_inst, ui
         if (cfg.cluster_size) {
             if ((rc = plan_launch_cluster(b.get()))) return rc;
         } else if (cfg.lowering == SIM_LOWER_GENERATED) {
-            if ((rc = ensure_loaded(nl, b->mode))) return rc;
+            // the module whose process functions carry digest code only when
+            // this batch keeps per-cycle digests
+            const bool dig = cfg.digest_capacity > 0;
+            if ((rc = ensure_loaded(nl, b->mode, dig))) return rc;
             b->generated = true;
-            b->gen_kernel[0] = reinterpret_cast<const void*>(nl->gen[b->mode].kernel[0]);
-            b->gen_kernel[1] = reinterpret_cast<const void*>(nl->gen[b->mode].kernel[1]);
+            b->gen_kernel[dig] = reinterpret_cast<const void*>(nl->gen[b->mode][dig].kernel);
             if ((rc = b->P_dev.alloc(sizeof(DevProg))) || (rc = b->S_dev.alloc(sizeof(DevState))) ||
                 (rc = b->h2d(b->P_dev.p, &b->P, sizeof(DevProg))) || (rc = plan_launch_gen(b.get())))
                 return rc;

@@ -272,13 +272,15 @@ __device__ __forceinline__ void gen_cycles(const DevProg* __restrict__ Pg, const
 #define RTLSIM_GEN_MAX_THREADS 1024
 #endif
 
-#define RTLSIM_GEN_KERNELS(MODE)                                                                              \
+// One kernel per generated module: rtl_gen_d1 (digests on) calls process
+// functions that carry the digest code, rtl_gen_d0 calls ones without it.
+#define RTLSIM_GEN_KERNEL_NAME_false rtl_gen_d0
+#define RTLSIM_GEN_KERNEL_NAME_true rtl_gen_d1
+#define RTLSIM_GEN_CAT(a, b) a##b
+#define RTLSIM_GEN_KERNEL(MODE, DIGEST)                                                                       \
     extern "C" __global__ void __launch_bounds__(RTLSIM_GEN_MAX_THREADS)                                      \
-        rtl_gen_d0(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
-        rtl::gen_cycles<MODE, false>(P, S, A);                                                                \
-    }                                                                                                         \
-    extern "C" __global__ void __launch_bounds__(RTLSIM_GEN_MAX_THREADS)                                      \
-        rtl_gen_d1(const rtl::DevProg* P, const rtl::DevState* S, rtl::LaunchArgs A) {                        \
-        rtl::gen_cycles<MODE, true>(P, S, A);                                                                 \
+        RTLSIM_GEN_CAT(RTLSIM_GEN_KERNEL_NAME_, DIGEST)(const rtl::DevProg* P, const rtl::DevState* S,        \
+                                                        rtl::LaunchArgs A) {                                  \
+        rtl::gen_cycles<MODE, DIGEST>(P, S, A);                                                               \
     }
 #endif
