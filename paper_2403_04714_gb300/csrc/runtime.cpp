@@ -46,12 +46,16 @@ int set_err(int code, const std::string& msg) {
     return code;
 }
 
+// On failure the runtime's last-error slot is read back (and so cleared), so
+// that a later launch check does not report this call's error again.
 #define CUDA_TRY(expr)                                                                        \
     do {                                                                                      \
         cudaError_t e_ = (expr);                                                              \
-        if (e_ != cudaSuccess)                                                                \
+        if (e_ != cudaSuccess) {                                                              \
+            (void)cudaGetLastError();                                                         \
             return set_err(e_ == cudaErrorMemoryAllocation ? SIM_ERR_OOM : SIM_ERR_CUDA,      \
                            std::string(#expr) + ": " + cudaGetErrorString(e_));               \
+        }                                                                                     \
     } while (0)
 
 uint64_t host_mix64(uint64_t z) {
@@ -481,7 +485,8 @@ int plan_launch_gen(sim_batch* b) {
     b->warps = warps;
     b->threads = warps * 32;
     int occ = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->gen_kernel[b->S.ring_cap > 0], b->threads, 0));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->gen_kernel[b->cfg.digest_capacity > 0],
+                                                           b->threads, 0));
     if (occ < 1) return set_err(SIM_ERR_CAPACITY, "generated kernel does not fit on an SM");
     b->max_grid = occ * sms;
     int need = int((b->n_tasks + warps - 1) / warps);
