@@ -177,9 +177,7 @@ def mesh_row(stream, flush):
     text = open(netgen.cached_netlist("mesh"), "rb").read()
     out = {}
     for name, cfg in (("grid_barrier", dict(target_processes=1216, warps_per_cta=8)),
-                      ("cluster", dict(cluster_size=2, warps_per_cta=8)),
-                      ("cluster_pairs", dict(cluster_size=2, warps_per_cta=8, chain=2)),
-                      ("grid_barrier_w4_pairs", dict(target_processes=608, warps_per_cta=4, chain=2))):
+                      ("cluster", dict(cluster_size=2, warps_per_cta=8))):
         try:
             nl = sim.Netlist(text, mode="lane_op", **cfg)
             b = sim.Batch(nl, 1, seed=42, stream=stream)
@@ -582,7 +580,7 @@ def main():
     ap.add_argument("--cycles", type=int, default=10_000, help="simulated cycles per step")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--ref-cycles", type=int, default=300)
-    ap.add_argument("--cpu-cycles", type=int, default=3000, help="oracle sample for cpu_baseline")
+    ap.add_argument("--cpu-cycles", type=int, default=10_000, help="oracle sample for cpu_baseline (~10 s)")
     ap.add_argument("--batched-cycles", type=int, default=1000)
     ap.add_argument("--no-rows", action="store_true", help="headline only (profiling runs)")
     ap.add_argument("--rows", default="single,batched,mesh,cluster,served",
