@@ -679,7 +679,8 @@ def main():
             if low == "generated":
                 # instances per CTA (32 x warps) and the task order, by measurement
                 cands = [dict(cfg_b, warps_per_cta=w, task_order=o)
-                         for w, o in ((8, "process_major"), (12, "process_major"), (8, "group_major"))]
+                         for w, o in ((12, "process_major"), (8, "process_major"), (6, "process_major"),
+                                      (4, "process_major"), (8, "group_major"))]
                 tuned_b = autotune.autotune(text, 4096, candidates=cands, cycles=40)
                 cfg_b = tuned_b["config"]
             nlb = sim.Netlist(text, kernel="persistent_graph", **cfg_b)

@@ -43,8 +43,11 @@ def _key(text: bytes, n_inst: int, device: str) -> str:
 
 def default_candidates(n_inst: int, sms: int = 152):
     if n_inst >= 32:
-        return [dict(mode="lane_inst", lowering="generated", warps_per_cta=w, task_order=o)
-                for w in (8, 4) for o in ("process_major", "group_major")]
+        # each warp's staging area of shared memory bounds the warps per SM:
+        # smaller CTAs let more of them share an SM
+        return ([dict(mode="lane_inst", lowering="generated", warps_per_cta=w, task_order="process_major")
+                 for w in (12, 8, 6, 4)] +
+                [dict(mode="lane_inst", lowering="generated", warps_per_cta=8, task_order="group_major")])
     # operator pairs chained in one step (chain=2) measured faster on every
     # geometry; the unchained adaptive geometry stays as the reference
     cands = [dict(mode="lane_op", lowering="bytecode", chain=0),              # adaptive: 4 or 8 per SM
