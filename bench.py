@@ -429,6 +429,7 @@ def served_full_row():
     kw = dict(pools=pools, shapes=shapes, cycles_hi=1e6, chunk=2000, pools_desc="8/4/2",
               large="4x4 mesh of 120k-op blocks (2M ops)")
     out = served_run(256, 200.0, persistent=1, **kw)
+    print(json.dumps({"served_full": out}), file=sys.stderr, flush=True)    # kept if the second run is cut short
     light = 0.7 * 256 / out["makespan_s"]
     out["rate_scaled"] = dict(served_run(256, light, persistent=1, **kw), arrival_rate_per_s=light)
     return out
