@@ -44,40 +44,11 @@ bool fits(const Netlist& nl, const Node& d) {
     }
 }
 
-// Register rows a process reads, staged in the warp's shared memory (lane =
-// instance): 64-bit rows (8 bytes a lane), then 32-bit rows (4 bytes a lane),
-// then 1-bit rows (one packed word for the warp's 32 instances).
-struct Stage {
-    std::vector<int32_t> off;     // per register: byte offset in the warp's area, -1 = not read
-    uint32_t bytes = 0;           // area size (multiple of 16)
-};
-
-Stage stage_layout(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p) {
-    Stage st;
-    st.off.assign(nl.reg_w.size(), -1);
-    std::vector<int32_t> regs;
-    for (int32_t f : part.procs[p])
-        for (int32_t n : part.fibers[f].nodes)
-            if (nl.nodes[n].op == OP_REG) regs.push_back(nl.nodes[n].a);
-    std::sort(regs.begin(), regs.end());
-    regs.erase(std::unique(regs.begin(), regs.end()), regs.end());
-    uint32_t at = 0;
-    for (int cls : {int(RC_W64), int(RC_W32), int(RC_BIT)})
-        for (int32_t r : regs)
-            if (L.cls[r] == cls) {
-                st.off[r] = int32_t(at);
-                at += cls == RC_W64 ? 256 : cls == RC_W32 ? 128 : 4;
-            }
-    st.bytes = (at + 15) & ~15u;
-    return st;
-}
-
 struct Emitter {
     const Netlist& nl;
     const RegLayout& L;
     int mode;
     bool digest;                  // emit the per-cycle digest terms
-    const Stage* stage;           // lane = instance: register rows staged in shared memory
     std::string& o;
     std::vector<int32_t> local;   // node -> local index (-1 = not in this process)
     std::vector<uint8_t> done;
@@ -103,12 +74,7 @@ struct Emitter {
         switch (d.op) {
         case OP_REG: {
             const uint32_t ix = L.idx[d.a];
-            if (stage) {
-                const std::string off = std::to_string(stage->off[d.a]);
-                if (L.cls[d.a] == RC_W64) e = "reinterpret_cast<const uint64_t*>(stg + " + off + ")[lane]";
-                else if (L.cls[d.a] == RC_W32) e = "reinterpret_cast<const uint32_t*>(stg + " + off + ")[lane]";
-                else e = "(*reinterpret_cast<const uint32_t*>(stg + " + off + ") >> lane) & 1u";
-            } else if (L.cls[d.a] == RC_W64) e = "c64[" + std::to_string(ix) + "ull * I + inst]";
+            if (L.cls[d.a] == RC_W64) e = "c64[" + std::to_string(ix) + "ull * I + inst]";
             else if (L.cls[d.a] == RC_W32) e = "c32[" + std::to_string(ix) + "ull * I + inst]";
             else if (mode == SIM_MODE_LANE_INST) e = "(c1[" + std::to_string(ix) + "ull * BS + g] >> lane) & 1u";
             else e = "c1[" + std::to_string(ix) + "ull * BS + inst]";
@@ -285,16 +251,11 @@ std::vector<int32_t> fiber_order(const Partition& part, size_t p, const std::vec
 
 void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p, int mode, bool digest,
                  std::string& o) {
-    // lane = instance: the process's register rows go through the warp's
-    // staging area (all copies in flight at once, then one wait)
-    const bool staged = mode == SIM_MODE_LANE_INST;
-    const Stage st = staged ? stage_layout(nl, part, L, p) : Stage();
     std::vector<int32_t> nodes;
     for (int32_t f : part.procs[p]) nodes.insert(nodes.end(), part.fibers[f].nodes.begin(), part.fibers[f].nodes.end());
     std::sort(nodes.begin(), nodes.end());
     nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
-    Emitter E{nl, L, mode, digest, staged ? &st : nullptr, o, std::vector<int32_t>(nl.nodes.size(), -1),
-              std::vector<uint8_t>(nodes.size(), 0)};
+    Emitter E{nl, L, mode, digest, o, std::vector<int32_t>(nl.nodes.size(), -1), std::vector<uint8_t>(nodes.size(), 0)};
     bool has_input = false;
     for (size_t i = 0; i < nodes.size(); i++) {
         E.local[nodes[i]] = int32_t(i);
@@ -313,21 +274,6 @@ void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, s
          "    const uint32_t* __restrict__ c1 = S.bits[par];\n    uint32_t* __restrict__ n1 = S.bits[nxt];\n"
          "    (void)c64; (void)n64; (void)c32; (void)n32; (void)c1; (void)n1; (void)BS; (void)lane; (void)pending;\n";
     if (has_input) o += "    const uint64_t key = S.key[inst];\n";
-    if (staged) {
-        o += "    unsigned char* const stg = rtl_gen_smem + (threadIdx.x >> 5) * RTLSIM_STAGE_BYTES;\n"
-             "    __syncwarp();   // the previous task's reads of the area are done\n";
-        for (size_t r = 0; r < nl.reg_w.size(); r++) {
-            if (st.off[r] < 0) continue;
-            const std::string off = std::to_string(st.off[r]), ix = std::to_string(L.idx[r]);
-            if (L.cls[r] == RC_W64)
-                o += "    stage_copy(stg + " + off + " + lane * 8u, c64 + " + ix + "ull * I + inst, 8);\n";
-            else if (L.cls[r] == RC_W32)
-                o += "    stage_copy(stg + " + off + " + lane * 4u, c32 + " + ix + "ull * I + inst, 4);\n";
-            else
-                o += "    if (lane == 0) stage_copy(stg + " + off + ", c1 + " + ix + "ull * BS + g, 4);\n";
-        }
-        o += "    stage_wait();\n    __syncwarp();\n";
-    }
     for (int32_t f : part.procs[p])
         if (part.fibers[f].mem >= 0) E.commit(part.fibers[f].mem);
     for (int32_t f : fiber_order(part, p, E.local, nodes.size())) {
@@ -349,17 +295,11 @@ void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, s
 }
 
 int gen_cuda(const Netlist& nl, const Partition& part, int mode, bool digest, int n_chunks, std::vector<GenUnit>& out,
-             uint32_t* stage_bytes, std::string& err) {
+             std::string& err) {
     (void)err;
     const RegLayout L = reg_layout(nl);
     const size_t NP = part.procs.size();
     out.clear();
-    // per-warp staging area: the largest process's register rows (lane = instance)
-    uint32_t stage = 16;
-    if (mode == SIM_MODE_LANE_INST)
-        for (size_t q = 0; q < NP; q++) stage = std::max(stage, stage_layout(nl, part, L, q).bytes);
-    *stage_bytes = mode == SIM_MODE_LANE_INST ? stage : 0;
-    const std::string prelude = "#define RTLSIM_STAGE_BYTES " + std::to_string(stage) + "u\n";
     const std::string proto = "(const rtl::DevProg* __restrict__, const rtl::DevState* __restrict__, uint32_t, uint64_t, "
                               "bool, uint32_t, uint64_t* __restrict__, int32_t)";
     // chunks of process functions, balanced by node count
@@ -374,7 +314,7 @@ int gen_cuda(const Netlist& nl, const Partition& part, int mode, bool digest, in
     for (int c = 0; c < n_chunks && p < NP; c++) {
         GenUnit u;
         u.name = "rtl_chunk" + std::to_string(c) + ".cu";
-        u.source = "#define RTLSIM_GENERATED 1\n" + prelude + "#include \"sim_rt.cuh\"\n\n";
+        u.source = "#include \"sim_rt.cuh\"\n\n";
         uint64_t goal = total * uint64_t(c + 1) / uint64_t(n_chunks), acc = 0;
         for (size_t q = 0; q < p; q++) acc += weight[q];
         do {
@@ -387,7 +327,7 @@ int gen_cuda(const Netlist& nl, const Partition& part, int mode, bool digest, in
     // dispatcher and kernels
     GenUnit k;
     k.name = "rtl_kernels.cu";
-    k.source = "#define RTLSIM_GENERATED 1\n" + prelude + "#include \"sim_rt.cuh\"\n\n";
+    k.source = "#define RTLSIM_GENERATED 1\n#include \"sim_rt.cuh\"\n\n";
     for (size_t q = 0; q < NP; q++) k.source += "extern \"C\" __device__ void rtl_p" + std::to_string(q) + proto + ";\n";
     k.source += "\nextern \"C\" __device__ void rtl_dispatch(uint32_t p, const rtl::DevProg* __restrict__ P, "
                 "const rtl::DevState* __restrict__ S, uint32_t g, uint64_t t, bool pending, uint32_t lane, "

@@ -17,10 +17,8 @@ struct GenUnit {
 // one kernel for lane mapping `mode`: rtl_gen_d1 with the per-cycle digest
 // code in every process function, or rtl_gen_d0 without any (its process
 // functions are that much shorter, which the instruction caches feel).
-// *stage_bytes receives the per-warp shared-memory staging area of the lane =
-// instance code (the largest process's register rows; 0 for LANE_OP).
 int gen_cuda(const Netlist& nl, const Partition& part, int mode, bool digest, int n_chunks, std::vector<GenUnit>& out,
-             uint32_t* stage_bytes, std::string& err);
+             std::string& err);
 void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, size_t p, int mode, bool digest,
                  std::string& o);
 

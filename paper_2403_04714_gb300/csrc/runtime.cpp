@@ -145,7 +145,6 @@ struct sim_netlist {
     rtl::GenModule gen[3][2];
     double gen_seconds[3][2] = {};
     bool gen_cached[3][2] = {};
-    uint32_t gen_stage[3][2] = {};        // per-warp staging bytes of the lane = instance code
     ~sim_netlist() {
         for (auto& gm : gen)
             for (auto& g : gm) rtl::jit_unload(g);
@@ -436,8 +435,7 @@ int ensure_compiled(sim_netlist* h, int mode, bool digest) {
     std::string err;
     unsigned hw = std::max(1u, std::thread::hardware_concurrency());
     int chunks = int(std::min<size_t>(std::max<size_t>(1, h->part.procs.size() / 16), size_t(hw) * 2));
-    uint32_t stage = 0;
-    int rc = rtl::gen_cuda(h->nl, h->part, mode, digest, chunks, units, &stage, err);
+    int rc = rtl::gen_cuda(h->nl, h->part, mode, digest, chunks, units, err);
     if (rc) return set_err(rc, err);
     if (const char* dump = getenv("RTLSIM_GEN_DUMP")) {     // developer aid: keep the generated sources
         for (auto& u : units) {
@@ -460,7 +458,6 @@ int ensure_compiled(sim_netlist* h, int mode, bool digest) {
     if (rc) return set_err(rc, err);
     h->gen_seconds[mode][digest] = sec;
     h->gen_cached[mode][digest] = cached;
-    h->gen_stage[mode][digest] = stage;
     return SIM_OK;
 }
 
@@ -482,21 +479,14 @@ int plan_launch_gen(sim_batch* b) {
     b->n_tasks = b->mode == SIM_MODE_LANE_INST ? n_proc * (b->I / 32) : n_proc * b->I;
     b->slot_words = 0;
     b->prog_words = 0;
-    // generated kernels: up to 1024 threads per CTA at 64 registers per thread;
-    // lane = instance code stages each task's register rows in a per-warp
-    // area of dynamic shared memory
+    b->smem = 0;
+    // generated kernels: up to 1024 threads per CTA at 64 registers per thread
     int warps = std::min(32, b->cfg.warps_per_cta ? int(b->cfg.warps_per_cta) : 8);
-    const bool dig = b->cfg.digest_capacity > 0;
-    const size_t stage = b->nl->gen_stage[b->mode][dig];
-    while (warps > 1 && size_t(warps) * stage > smem_limit()) warps /= 2;
-    if (size_t(warps) * stage > smem_limit()) return set_err(SIM_ERR_CAPACITY, "staging area exceeds shared memory");
     b->warps = warps;
     b->threads = warps * 32;
-    b->smem = size_t(warps) * stage;
-    if (b->smem > 48 * 1024)
-        CUDA_TRY(cudaFuncSetAttribute(b->gen_kernel[dig], cudaFuncAttributeMaxDynamicSharedMemorySize, int(b->smem)));
     int occ = 0;
-    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->gen_kernel[dig], b->threads, b->smem));
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, b->gen_kernel[b->cfg.digest_capacity > 0],
+                                                           b->threads, 0));
     if (occ < 1) return set_err(SIM_ERR_CAPACITY, "generated kernel does not fit on an SM");
     b->max_grid = occ * sms;
     int need = int((b->n_tasks + warps - 1) / warps);
@@ -523,8 +513,8 @@ cudaError_t launch_any(sim_batch* b, bool cooperative, int grid, const LaunchArg
     const DevState* Sd = b->S_dev.as<DevState>();
     LaunchArgs a = A;
     void* args[] = {&Pd, &Sd, &a};
-    if (cooperative) return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(b->threads), args, b->smem, b->stream);
-    return cudaLaunchKernel(f, dim3(grid), dim3(b->threads), args, b->smem, b->stream);
+    if (cooperative) return cudaLaunchCooperativeKernel(f, dim3(grid), dim3(b->threads), args, 0, b->stream);
+    return cudaLaunchKernel(f, dim3(grid), dim3(b->threads), args, 0, b->stream);
 }
 
 // Largest sum of compact-program sizes over the processes one warp owns

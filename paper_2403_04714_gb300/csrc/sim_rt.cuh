@@ -191,23 +191,7 @@ static __device__ void final_commit(const DevProg& P, const DevState& S, uint64_
 // Kernels for generated code (compiled at run time with the generated units).
 // The per-process functions rtl_p<k> and the dispatcher come from codegen.cpp.
 // ---------------------------------------------------------------------------
-// Asynchronous copies of register rows into a warp's shared-memory staging
-// area (generated lane = instance code): the copies of a process's whole read
-// set are in flight at once, then one wait.
-__device__ __forceinline__ void stage_copy(void* smem, const void* gmem, int bytes) {
-    const uint32_t s = uint32_t(__cvta_generic_to_shared(smem));
-    uint64_t g;
-    asm("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(gmem));
-    if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(g) : "memory");
-    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(g) : "memory");
-}
-__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-
 #ifdef RTLSIM_GENERATED
-// Dynamic shared memory of a generated lane = instance kernel: one staging
-// area of RTLSIM_STAGE_BYTES per warp.
-extern __shared__ __align__(16) unsigned char rtl_gen_smem[];
-
 extern "C" __device__ void rtl_dispatch(uint32_t p, const rtl::DevProg* __restrict__ P,
                                         const rtl::DevState* __restrict__ S, uint32_t g, uint64_t t, bool pending,
                                         uint32_t lane, uint64_t* __restrict__ dacc, int32_t col);
