@@ -140,6 +140,7 @@ struct LaunchArgs {
     uint32_t mirror_off;        // start of the mirror in a cluster CTA's shared memory (64-bit words)
     uint32_t grid;              // launch shape the batch planned (checked by the cluster kernel on entry)
     uint32_t smem_bytes;        // dynamic shared memory the batch planned
+    uint32_t pairs;             // the LANE_OP programs hold operator pair steps
 };
 
 }  // namespace rtl

@@ -369,7 +369,9 @@ __device__ __forceinline__ uint64_t eval_op(const Dec& d, uint64_t a, uint64_t b
 // lanes past the step's count repeat its first instruction and write the
 // spare slot `dummy` (the last word of the warp's slot region), which no
 // instruction reads.
-template <bool DIGEST>
+// PAIRS: the program was lowered with operator pairs, whose steps are tested
+// first (a program without them never pays that test).
+template <bool DIGEST, bool PAIRS>
 __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p, uint32_t inst, uint64_t t,
                                  bool pending, uint64_t* __restrict__ sl, const uint32_t* __restrict__ prog,
                                  uint32_t lane, uint32_t dummy, const uint64_t* mir_cur = nullptr,
@@ -384,26 +386,30 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     for (uint32_t b = 0; b < nb; b++) {
         const uint32_t e_next = b + 1 < nb ? table[b + 1] : 0;
         const uint32_t first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        if (!(e & kStepGeneric)) {
-            // operator step: all 32 lanes, no branch (idle lanes write the spare slot)
-            const bool on = lane < cnt;
-            const Dec d = decode(ins[on ? first + lane : first]);
-            sl[on ? d.dst : dummy] = eval_op(d, sl[d.a], sl[d.b], sl[d.c]);
-        } else if (e & kStepChain) {
+        if (PAIRS && (e & kStepChain)) {
             // two rows: each lane's first operator, then its second one (no
             // warp barrier between them); imm bits 0/1/2 take operands a/b/c
-            // of the second from the first result
+            // of the second from the first result.  The second row's slot
+            // operands hold values of earlier steps (a slot written in this
+            // step is never read here except through the flags), so they are
+            // loaded together with the first row's, before its store.
             const uint32_t n = cnt >> 1;
             const bool on = lane < n;
             const uint32_t i1 = on ? first + lane : first;
             const Dec d1 = decode(ins[i1]);
             const Dec d2 = decode(ins[i1 + n]);
-            const uint64_t r1 = eval_op(d1, sl[d1.a], sl[d1.b], sl[d1.c]);
+            const uint64_t a1 = sl[d1.a], b1 = sl[d1.b], c1 = sl[d1.c];
+            const uint64_t a2s = sl[d2.a], b2s = sl[d2.b], c2s = sl[d2.c];
+            const uint64_t r1 = eval_op(d1, a1, b1, c1);
+            const uint64_t r2 = eval_op(d2, (d2.imm & 1u) ? r1 : a2s, (d2.imm & 2u) ? r1 : b2s,
+                                        (d2.imm & 4u) ? r1 : c2s);
             sl[on ? d1.dst : dummy] = r1;
-            const uint64_t a2 = (d2.imm & 1u) ? r1 : sl[d2.a];
-            const uint64_t b2 = (d2.imm & 2u) ? r1 : sl[d2.b];
-            const uint64_t c2 = (d2.imm & 4u) ? r1 : sl[d2.c];
-            sl[on && d2.op != D_NOP ? d2.dst : dummy] = eval_op(d2, a2, b2, c2);
+            sl[on && d2.op != D_NOP ? d2.dst : dummy] = r2;
+        } else if (!(e & kStepGeneric)) {
+            // operator step: all 32 lanes, no branch (idle lanes write the spare slot)
+            const bool on = lane < cnt;
+            const Dec d = decode(ins[on ? first + lane : first]);
+            sl[on ? d.dst : dummy] = eval_op(d, sl[d.a], sl[d.b], sl[d.c]);
         } else if (e & kStepLeaf) {
             // up to four leaves per lane, every load in flight before the
             // first value is stored; idle lanes write the spare slot
@@ -432,7 +438,7 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
 
-template <int MODE, bool DIGEST>
+template <int MODE, bool DIGEST, bool PAIRS>
 __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
     const uint32_t lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -463,7 +469,7 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
             uint32_t off = 0;
             for (uint32_t p = warp; p < P.n_proc; p += tw) {
                 for (uint32_t g = 0; g < S.I; g++)
-                    task_lane_op_res<DIGEST>(P, S, p, g, t, pending, sl, prog + off, lane, A.slot_words - 1);
+                    task_lane_op_res<DIGEST, PAIRS>(P, S, p, g, t, pending, sl, prog + off, lane, A.slot_words - 1);
                 off += P.c_size[p];
             }
         } else {
@@ -492,7 +498,7 @@ __global__ void __launch_bounds__(1024) k_cycles(DevProg P, DevState S, LaunchAr
 // Mirror buffer t&1 holds cycle t's values; at launch it is filled from the
 // global state, which producers keep writing for readers in other clusters,
 // for the host and for the next launch.
-template <bool DIGEST>
+template <bool DIGEST, bool PAIRS>
 __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, LaunchArgs A) {
     extern __shared__ __align__(16) uint64_t smem[];
     __shared__ __align__(8) uint64_t cbar[2];
@@ -543,9 +549,9 @@ __global__ void __launch_bounds__(1024) k_cycles_cl(DevProg P, DevState S, Launc
         if (rec && threadIdx.x == 0) rec[0] = globaltimer_ns();
         if (p != kNoProc) {
             const uint32_t par = uint32_t(t & 1);
-            task_lane_op_res<DIGEST>(P, S, p, 0, t, pending, sl, prog, lane, slot_words - 1,
-                                     mirror + (uint64_t)par * A.mirror_words,
-                                     smem_addr(mirror + (uint64_t)(par ^ 1) * A.mirror_words));
+            const uint64_t* mc = mirror + (uint64_t)par * A.mirror_words;
+            const uint32_t mn = smem_addr(mirror + (uint64_t)(par ^ 1) * A.mirror_words);
+            task_lane_op_res<DIGEST, PAIRS>(P, S, p, 0, t, pending, sl, prog, lane, slot_words - 1, mc, mn);
         }
         const bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
         if (A.one_cluster && A.skip_cta < 0) {
@@ -645,12 +651,16 @@ __global__ void k_state_digest(DevProg P, DevState S, uint32_t par, const uint64
 // ---------------------------------------------------------------------------
 // Host-side launchers
 // ---------------------------------------------------------------------------
-template <int MODE, bool DIGEST>
-static void* kfun() { return reinterpret_cast<void*>(&k_cycles<MODE, DIGEST>); }
+template <int MODE, bool DIGEST, bool PAIRS>
+static void* kfun() { return reinterpret_cast<void*>(&k_cycles<MODE, DIGEST, PAIRS>); }
 
-static void* cycles_fn(int mode, bool digest) {
-    if (mode == SIM_MODE_LANE_INST) return digest ? kfun<SIM_MODE_LANE_INST, true>() : kfun<SIM_MODE_LANE_INST, false>();
-    return digest ? kfun<SIM_MODE_LANE_OP, true>() : kfun<SIM_MODE_LANE_OP, false>();
+// The kernel for a lane mapping, digests on or off, and (LANE_OP) programs
+// with or without operator pairs.
+static void* cycles_fn(int mode, bool digest, bool pairs) {
+    if (mode == SIM_MODE_LANE_INST)
+        return digest ? kfun<SIM_MODE_LANE_INST, true, false>() : kfun<SIM_MODE_LANE_INST, false, false>();
+    if (pairs) return digest ? kfun<SIM_MODE_LANE_OP, true, true>() : kfun<SIM_MODE_LANE_OP, false, true>();
+    return digest ? kfun<SIM_MODE_LANE_OP, true, false>() : kfun<SIM_MODE_LANE_OP, false, false>();
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by every
@@ -658,24 +668,32 @@ static void* cycles_fn(int mode, bool digest) {
 // smaller batch never lowers it under a larger one.
 cudaError_t prepare_cycles_kernel(int mode, size_t smem) {
     static std::mutex mu;
-    static size_t set_to[3][2] = {};
+    static size_t set_to[3][2][2] = {};
     std::lock_guard<std::mutex> g(mu);
-    for (int d = 0; d < 2; d++) {
-        if (smem <= set_to[mode][d]) continue;
-        cudaError_t e = cudaFuncSetAttribute(cycles_fn(mode, d), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        if (e != cudaSuccess) return e;
-        set_to[mode][d] = smem;
-    }
+    for (int d = 0; d < 2; d++)
+        for (int q = 0; q < 2; q++) {
+            if (smem <= set_to[mode][d][q]) continue;
+            cudaError_t e =
+                cudaFuncSetAttribute(cycles_fn(mode, d, q), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+            if (e != cudaSuccess) return e;
+            set_to[mode][d][q] = smem;
+        }
     return cudaSuccess;
 }
 
+// (the variants with and without pairs fit alike: the lower of the two)
 cudaError_t occupancy_cycles(int mode, int threads, size_t smem, int* blocks_per_sm) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, cycles_fn(mode, false), threads, smem);
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, cycles_fn(mode, false, false), threads, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, cycles_fn(mode, false, true), threads, smem);
+    *blocks_per_sm = a < b ? a : b;
+    return e;
 }
 
 cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int threads, size_t smem, cudaStream_t st,
                           const DevProg& P, const DevState& S, const LaunchArgs& A) {
-    void* f = cycles_fn(mode, digest);
+    void* f = cycles_fn(mode, digest, A.pairs != 0);
     DevProg p = P;
     DevState s = S;
     LaunchArgs a = A;
@@ -684,27 +702,29 @@ cudaError_t launch_cycles(int mode, bool digest, bool cooperative, int grid, int
     return cudaLaunchKernel(f, dim3(grid), dim3(threads), args, smem, st);
 }
 
-static void* cycles_cl_fn(bool digest) {
-    return digest ? reinterpret_cast<void*>(&k_cycles_cl<true>) : reinterpret_cast<void*>(&k_cycles_cl<false>);
+static void* cycles_cl_fn(bool digest, bool pairs) {
+    if (pairs) return digest ? reinterpret_cast<void*>(&k_cycles_cl<true, true>) : reinterpret_cast<void*>(&k_cycles_cl<false, true>);
+    return digest ? reinterpret_cast<void*>(&k_cycles_cl<true, false>) : reinterpret_cast<void*>(&k_cycles_cl<false, false>);
 }
 
 // Shared-memory limit (monotonic, as for k_cycles) and, above the portable
 // cluster size of 8, the non-portable cluster size opt-in.
 cudaError_t prepare_cluster_kernel(size_t smem, uint32_t C) {
     static std::mutex mu;
-    static size_t set_to[2] = {0, 0};
-    static bool nonportable[2] = {false, false};
+    static size_t set_to[4] = {0, 0, 0, 0};
+    static bool nonportable[4] = {false, false, false, false};
     std::lock_guard<std::mutex> g(mu);
-    for (int d = 0; d < 2; d++) {
-        if (smem > set_to[d]) {
-            cudaError_t e = cudaFuncSetAttribute(cycles_cl_fn(d), cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    for (int v = 0; v < 4; v++) {
+        void* f = cycles_cl_fn(v & 1, v >> 1);
+        if (smem > set_to[v]) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
             if (e != cudaSuccess) return e;
-            set_to[d] = smem;
+            set_to[v] = smem;
         }
-        if (C > 8 && !nonportable[d]) {
-            cudaError_t e = cudaFuncSetAttribute(cycles_cl_fn(d), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (C > 8 && !nonportable[v]) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
-            nonportable[d] = true;
+            nonportable[v] = true;
         }
     }
     return cudaSuccess;
@@ -730,7 +750,11 @@ static cudaLaunchConfig_t cluster_config(int grid, int threads, size_t smem, uin
 cudaError_t occupancy_clusters(int grid, int threads, size_t smem, uint32_t C, int* n_clusters) {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, nullptr, at);
-    return cudaOccupancyMaxActiveClusters(n_clusters, cycles_cl_fn(false), &cfg);
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&a, cycles_cl_fn(false, false), &cfg);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&b, cycles_cl_fn(false, true), &cfg);
+    *n_clusters = a < b ? a : b;
+    return e;
 }
 
 // A grid of several clusters synchronises with the grid barrier, so all of
@@ -747,7 +771,7 @@ cudaError_t launch_cycles_cl(bool digest, int grid, int threads, size_t smem, ui
     void* args[] = {&p, &s, &a};
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = cluster_config(grid, threads, smem, C, st, at);
-    return cudaLaunchKernelExC(&cfg, cycles_cl_fn(digest), args);
+    return cudaLaunchKernelExC(&cfg, cycles_cl_fn(digest, A.pairs != 0), args);
 }
 
 cudaError_t launch_commit(int grid, cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t_end,

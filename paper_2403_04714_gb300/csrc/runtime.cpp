@@ -855,6 +855,7 @@ LaunchArgs base_args(sim_batch* b) {
     A.proc_major = b->proc_major;
     A.wave_groups = b->wave_groups;
     A.cta_major = b->cta_major;
+    A.pairs = b->nl->cfg.chain >= 2 ? 1u : 0u;
     if (b->cluster) {
         A.cluster = b->nl->cplan.C;
         A.mirror_words = b->nl->cplan.mirror_words;
