@@ -1471,8 +1471,9 @@ int append_program(const std::vector<CStep>& steps, std::vector<uint32_t>& words
 // Measured on the mid netlist (one GB300, 4-CTA clusters): pairs take the
 // slowest process from 66 to 40 steps and the rate from 77-78k to 83-84k
 // cycles/s; chains of three or four (31 and 28 steps) gain nothing more,
-// because a step costs about as much to enter (instruction and operand loads,
-// store, warp barrier) as one more operator costs to evaluate.  A variant
+// because every lane of a step pays for its longest chain: a chained
+// operator saves one step entry but adds a row (a decode, operand loads, a
+// store and an evaluation) to the whole step.  A variant
 // that kept only the pairs' second operators (no D_NOP, lanes with a pair
 // first) made smaller programs but measured 4 % slower on the same GPU
 // (79.3k against 82.6k cycles/s), so the rows stay full.
