@@ -383,29 +383,53 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
     const uint32_t* table = prog + 1;
     const uint4* ins = reinterpret_cast<const uint4*>(prog + ((nb + 4) & ~3u));
     uint32_t e = nb ? table[0] : 0;
-    for (uint32_t b = 0; b < nb; b++) {
+    for (uint32_t b = 0; b < nb;) {
+        if (PAIRS) {
+            // a run of pair steps (most of a pair program) in a loop of its own:
+            // no step-kind dispatch on this path
+            while (e & kStepChain) {
+                // two rows: each lane's first operator, then its second one (no
+                // warp barrier between them); imm bits 0/1/2 take operands
+                // a/b/c of the second from the first result.  The second row's
+                // slot operands hold values of earlier steps (a slot written in
+                // this step is never read here except through the flags), so
+                // they are loaded together with the first row's, before its
+                // store.
+                const uint32_t e_next = b + 1 < nb ? table[b + 1] : 0;
+                const uint32_t first = e & 0xffff, n = ((e >> 16) & kStepCountMask) >> 1;
+                const bool on = lane < n;
+                const uint32_t i1 = on ? first + lane : first;
+                const Dec d1 = decode(ins[i1]);
+                const Dec d2 = decode(ins[i1 + n]);
+                const uint64_t a1 = sl[d1.a], b1 = sl[d1.b], c1 = sl[d1.c];
+                const uint64_t a2s = sl[d2.a], b2s = sl[d2.b], c2s = sl[d2.c];
+                const uint64_t r1 = eval_op(d1, a1, b1, c1);
+                const uint64_t r2 = eval_op(d2, (d2.imm & 1u) ? r1 : a2s, (d2.imm & 2u) ? r1 : b2s,
+                                            (d2.imm & 4u) ? r1 : c2s);
+                sl[on ? d1.dst : dummy] = r1;
+                sl[on && d2.op != D_NOP ? d2.dst : dummy] = r2;
+                __syncwarp();
+                e = e_next;
+                b++;
+            }
+            if (b >= nb) break;
+        } else {
+            // a run of operator steps in a loop of its own likewise
+            while (!(e & kStepGeneric) && b < nb) {
+                const uint32_t e_next = b + 1 < nb ? table[b + 1] : 0;
+                const uint32_t first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
+                const bool on = lane < cnt;
+                const Dec d = decode(ins[on ? first + lane : first]);
+                sl[on ? d.dst : dummy] = eval_op(d, sl[d.a], sl[d.b], sl[d.c]);
+                __syncwarp();
+                e = e_next;
+                b++;
+            }
+            if (b >= nb) break;
+        }
         const uint32_t e_next = b + 1 < nb ? table[b + 1] : 0;
         const uint32_t first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        if (PAIRS && (e & kStepChain)) {
-            // two rows: each lane's first operator, then its second one (no
-            // warp barrier between them); imm bits 0/1/2 take operands a/b/c
-            // of the second from the first result.  The second row's slot
-            // operands hold values of earlier steps (a slot written in this
-            // step is never read here except through the flags), so they are
-            // loaded together with the first row's, before its store.
-            const uint32_t n = cnt >> 1;
-            const bool on = lane < n;
-            const uint32_t i1 = on ? first + lane : first;
-            const Dec d1 = decode(ins[i1]);
-            const Dec d2 = decode(ins[i1 + n]);
-            const uint64_t a1 = sl[d1.a], b1 = sl[d1.b], c1 = sl[d1.c];
-            const uint64_t a2s = sl[d2.a], b2s = sl[d2.b], c2s = sl[d2.c];
-            const uint64_t r1 = eval_op(d1, a1, b1, c1);
-            const uint64_t r2 = eval_op(d2, (d2.imm & 1u) ? r1 : a2s, (d2.imm & 2u) ? r1 : b2s,
-                                        (d2.imm & 4u) ? r1 : c2s);
-            sl[on ? d1.dst : dummy] = r1;
-            sl[on && d2.op != D_NOP ? d2.dst : dummy] = r2;
-        } else if (!(e & kStepGeneric)) {
+        if (!(e & kStepGeneric)) {
             // operator step: all 32 lanes, no branch (idle lanes write the spare slot)
             const bool on = lane < cnt;
             const Dec d = decode(ins[on ? first + lane : first]);
@@ -434,6 +458,7 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
         }
         __syncwarp();
         e = e_next;
+        b++;
     }
     finish_lane_op<DIGEST>(S, p, inst, t, col, lane, dacc);
 }
