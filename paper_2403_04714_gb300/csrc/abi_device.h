@@ -108,6 +108,7 @@ struct DevState {
     const uint64_t* rom_dig;    // digest of the memories without write ports, per instance
     uint32_t* bar;              // grid barrier words: [0] arrivals, [1] generation
     int32_t* err;               // first error code of the launch (0 = none)
+    uint64_t* stim[2];          // generated code: input k of instance i at cycle t in stim[t & 1][k * I + i], or null
     uint32_t I;                 // instances (padded to the lane-group size)
     uint32_t pack;              // instances per bit word (32 LANE_INST, 1 LANE_OP)
     uint32_t bit_stride;        // words per 1-bit register

@@ -80,8 +80,8 @@ struct Emitter {
             else e = "c1[" + std::to_string(ix) + "ull * BS + inst]";
             break;
         }
-        case OP_INPUT:
-            e = "(" + T + ")stimulus(P, S, key, " + std::to_string(d.a) + "u, inst, t, " + std::to_string(d.w) + "u)";
+        case OP_INPUT:      // the value filled for this cycle (already reduced to the input's width)
+            e = "(" + T + ")stv[" + std::to_string(d.a) + "ull * I + inst]";
             break;
         case OP_MEMRD:
             e = "(" + T + ")mem_read(P, S, " + std::to_string(d.a) + "u, " + ref64(d.b) + " & " +
@@ -273,7 +273,7 @@ void gen_process(const Netlist& nl, const Partition& part, const RegLayout& L, s
          "    const uint32_t* __restrict__ c32 = S.w32[par];\n    uint32_t* __restrict__ n32 = S.w32[nxt];\n"
          "    const uint32_t* __restrict__ c1 = S.bits[par];\n    uint32_t* __restrict__ n1 = S.bits[nxt];\n"
          "    (void)c64; (void)n64; (void)c32; (void)n32; (void)c1; (void)n1; (void)BS; (void)lane; (void)pending;\n";
-    if (has_input) o += "    const uint64_t key = S.key[inst];\n";
+    if (has_input) o += "    const uint64_t* __restrict__ stv = S.stim[par];\n";
     for (int32_t f : part.procs[p])
         if (part.fibers[f].mem >= 0) E.commit(part.fibers[f].mem);
     for (int32_t f : fiber_order(part, p, E.local, nodes.size())) {

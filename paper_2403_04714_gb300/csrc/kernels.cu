@@ -20,6 +20,7 @@
 //             1-bit registers packed 32 instances per word with __ballot_sync.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -602,6 +603,13 @@ __global__ void k_commit(DevProg P, DevState S, uint64_t t_end, const uint64_t* 
     final_commit(P, S, t_end, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
 }
 
+// Input values of a step's first cycle (generated code), before its first
+// cycle launch; the cycle base is read from device memory in graph replays.
+__global__ void k_stim(DevProg P, DevState S, uint64_t t, const uint64_t* t0_dev) {
+    if (t0_dev) t += *t0_dev;
+    fill_stim(P, S, t, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
+}
+
 // Advance the device-resident cycle base of a replayed graph chunk.
 __global__ void k_advance(uint64_t* t0_dev, uint64_t n) { *t0_dev += n; }
 
@@ -810,6 +818,13 @@ cudaError_t launch_reset_slots(cudaStream_t st, const DevProg& P, const DevState
                                uint64_t mem_words, const uint64_t* mem_init_dig, uint64_t rom_init_dig) {
     k_reset_slots<<<256, 256, 0, st>>>(P, S, par, lo, n, reg_init, mem_image, mem_word_off, mem_words, mem_init_dig,
                                        rom_init_dig);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stim(cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t, const uint64_t* t0_dev) {
+    const uint64_t n = (uint64_t)P.n_in * S.I;
+    if (!S.stim[0] || n == 0) return cudaSuccess;
+    k_stim<<<uint32_t(std::min<uint64_t>((n + 255) / 256, 4096)), 256, 0, st>>>(P, S, t, t0_dev);
     return cudaGetLastError();
 }
 

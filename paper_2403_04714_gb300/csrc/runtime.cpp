@@ -29,6 +29,7 @@ cudaError_t occupancy_clusters(int grid, int threads, size_t smem, uint32_t C, i
 cudaError_t launch_cycles_cl(bool digest, int grid, int threads, size_t smem, uint32_t C, cudaStream_t st,
                              const DevProg& P, const DevState& S, const LaunchArgs& A);
 cudaError_t launch_advance(cudaStream_t st, uint64_t* t0_dev, uint64_t n);
+cudaError_t launch_stim(cudaStream_t st, const DevProg& P, const DevState& S, uint64_t t, const uint64_t* t0_dev);
 cudaError_t launch_set_u64(cudaStream_t st, uint64_t* p, uint64_t v);
 cudaError_t launch_state_digest(cudaStream_t st, const DevProg& P, const DevState& S, uint32_t par,
                                 const uint64_t* mem_word_off, uint64_t mem_words, uint64_t* out, uint32_t n_inst);
@@ -180,7 +181,7 @@ struct sim_batch {
     uint32_t mirror_off = 0;                // cluster CTA layout: mirror start (64-bit words)
     // state
     DBuf bits[2], w32[2], w64[2], mem, rec[2], key, hold_val, hold_flag, ring, track, mem_dig, rom_dig, bar, err, t0_dev,
-        scratch, P_dev, S_dev, phase;
+        scratch, P_dev, S_dev, phase, stim;
     uint32_t phase_n = 0, phase_grid = 0;   // phase timers of the last persistent launch
     DevProg P{};
     DevState S{};
@@ -905,6 +906,10 @@ int step_persistent(sim_batch* b, uint64_t n) {
     CUDA_TRY(cudaMemsetAsync(b->bar.p, 0, 8, b->stream));
     int rc = sync_state_view(b);
     if (rc) return rc;
+    if (b->S.stim[0]) {
+        CUDA_TRY(launch_stim(b->stream, b->P, b->S, b->cycle, nullptr));
+        b->kernels_launched++;
+    }
     CUDA_TRY(launch_any(b, true, b->grid, A));
     b->kernels_launched++;
     return SIM_OK;
@@ -937,6 +942,7 @@ int step_persistent_graph(sim_batch* b, uint64_t n) {
         A.pending_first = 0;
         A.grid_sync = 1;
         cudaError_t e = cudaMemsetAsync(b->bar.p, 0, 8, b->stream);
+        if (e == cudaSuccess) e = launch_stim(b->stream, b->P, b->S, 0, A.t0_dev);
         if (e == cudaSuccess) e = launch_any(b, true, b->grid, A);
         if (e == cudaSuccess) e = launch_advance(b->stream, b->t0_dev.as<uint64_t>(), n);
         cudaError_t e2 = cudaStreamEndCapture(b->stream, &g);
@@ -950,7 +956,7 @@ int step_persistent_graph(sim_batch* b, uint64_t n) {
     }
     CUDA_TRY(launch_set_u64(b->stream, b->t0_dev.as<uint64_t>(), b->cycle));
     CUDA_TRY(cudaGraphLaunch(b->pgraph, b->stream));
-    b->kernels_launched += 3;
+    b->kernels_launched += b->S.stim[0] ? 4 : 3;
     return SIM_OK;
 }
 
@@ -961,6 +967,10 @@ int step_per_cycle(sim_batch* b, uint64_t n) {
     A.n = 1;
     A.grid_sync = 0;
     int grid = per_cycle_grid(b);
+    if (b->S.stim[0]) {
+        CUDA_TRY(launch_stim(b->stream, b->P, b->S, b->cycle, nullptr));
+        b->kernels_launched++;
+    }
     for (uint64_t k = 0; k < n; k++) {
         A.t0 = b->cycle + k;
         A.pending_first = k > 0;
@@ -990,7 +1000,7 @@ int step_graph(sim_batch* b, uint64_t n) {
         A.n = 1;
         A.grid_sync = 0;
         int grid = per_cycle_grid(b);
-        cudaError_t e = cudaSuccess;
+        cudaError_t e = launch_stim(b->stream, b->P, b->S, 0, A.t0_dev);
         for (uint32_t k = 0; k < chunk && e == cudaSuccess; k++) {
             A.t0 = k;
             A.pending_first = k > 0;
@@ -1012,7 +1022,7 @@ int step_graph(sim_batch* b, uint64_t n) {
     b->kernels_launched++;
     while (n - done >= chunk) {
         CUDA_TRY(cudaGraphLaunch(b->graph, b->stream));
-        b->kernels_launched += chunk + 2;
+        b->kernels_launched += chunk + (b->S.stim[0] ? 3 : 2);
         done += chunk;
     }
     if (done < n) {
@@ -1099,6 +1109,14 @@ int create_instances(sim_netlist* nl, const sim_config& cfg, uint32_t n_inst, ui
             if ((rc = ensure_loaded(nl, b->mode, dig))) return rc;
             b->generated = true;
             b->gen_kernel[dig] = reinterpret_cast<const void*>(nl->gen[b->mode][dig].kernel);
+            // the input values of the current and the next cycle (generated
+            // process functions read them instead of hashing every input)
+            const size_t n_in = nl->nl.in_w.size();
+            if (n_in) {
+                if ((rc = b->stim.alloc(2 * n_in * size_t(b->I) * 8))) return rc;
+                b->S.stim[0] = b->stim.as<uint64_t>();
+                b->S.stim[1] = b->S.stim[0] + n_in * size_t(b->I);
+            }
             if ((rc = b->P_dev.alloc(sizeof(DevProg))) || (rc = b->S_dev.alloc(sizeof(DevState))) ||
                 (rc = b->h2d(b->P_dev.p, &b->P, sizeof(DevProg))) || (rc = plan_launch_gen(b.get())))
                 return rc;
@@ -1550,7 +1568,9 @@ size_t pool_footprint(const sim_netlist* h, uint32_t capacity) {
     const RegLayout& L = h->layout;
     uint64_t I = (uint64_t(capacity) + 31) / 32 * 32;
     uint64_t per = 2 * (uint64_t(L.count[RC_W64]) * 8 + uint64_t(L.count[RC_W32]) * 4 + (L.count[RC_BIT] + 7) / 8);
-    per += h->mem_word_off.back() * 8 + nl.wports.size() * 32 + nl.in_w.size() * 9 + nl.mem_lg.size() * 8 + 40;
+    // memories, write records, held inputs (value + flag) and, with generated
+    // code, the input values of two cycles
+    per += h->mem_word_off.back() * 8 + nl.wports.size() * 32 + nl.in_w.size() * (9 + 16) + nl.mem_lg.size() * 8 + 40;
     uint64_t prog = (h->low.s_ins.size() + h->low.b_ins.size()) * 16 + h->low.c_words.size() * 4;
     return size_t(per * I + prog + 2 * h->mem_word_off.back() * 8);
 }

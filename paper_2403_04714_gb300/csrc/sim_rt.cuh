@@ -185,6 +185,21 @@ static __device__ void final_commit(const DevProg& P, const DevState& S, uint64_
     }
 }
 
+// Input values of cycle t for every (input, instance), k-major so that the
+// lanes of a generated process function (consecutive instances) read
+// consecutive words: each input is hashed once per instance and cycle instead
+// of once in every process that reads it (about 80 processes per input on the
+// 200k-op netlist).  Grid-stride over the calling threads.
+__device__ __forceinline__ void fill_stim(const DevProg& P, const DevState& S, uint64_t t, uint64_t tid,
+                                          uint64_t nth) {
+    uint64_t* out = S.stim[t & 1];
+    const uint64_t n = (uint64_t)P.n_in * S.I;
+    for (uint64_t e = tid; e < n; e += nth) {
+        const uint32_t k = uint32_t(e / S.I), inst = uint32_t(e % S.I);
+        out[e] = stimulus(P, S, S.key[inst], k, inst, t, P.in_w[k]);
+    }
+}
+
 }  // namespace rtl
 
 // ---------------------------------------------------------------------------
@@ -254,6 +269,10 @@ __device__ __forceinline__ void gen_cycles(const DevProg* __restrict__ Pg, const
                 __syncwarp();
             }
         }
+        // the next cycle's input values (read after the barrier, or by the next
+        // launch); the step's first cycle had its own filled before the launch
+        if (S.stim[0])
+            fill_stim(P, S, t + 1, (uint64_t)blockIdx.x * blockDim.x + threadIdx.x, (uint64_t)gridDim.x * blockDim.x);
         if (A.grid_sync) {
             const bool skip = (int32_t)blockIdx.x == A.skip_cta && c == 0;
             if (!grid_barrier(S.bar, gen, A.timeout_ns, S.err, skip, rec ? rec + 1 : nullptr)) return;
