@@ -678,10 +678,9 @@ def main():
             cfg_b = {"mode": "lane_inst", "lowering": low}
             tuned_b = None
             if low == "generated":
-                # instances per CTA (32 x warps) and the task order, by measurement
-                cands = [dict(cfg_b, warps_per_cta=w, task_order=o)
-                         for w, o in ((12, "process_major"), (8, "process_major"), (6, "process_major"),
-                                      (4, "process_major"), (8, "group_major"))]
+                # instances per CTA (32 x warps), the task order and the number
+                # of processes, by measurement (the autotuner's candidates)
+                cands = autotune.default_candidates(4096, torch.cuda.get_device_properties(0).multi_processor_count)
                 tuned_b = autotune.autotune(text, 4096, candidates=cands, cycles=40)
                 cfg_b = tuned_b["config"]
             nlb = sim.Netlist(text, kernel="persistent_graph", **cfg_b)
