@@ -108,7 +108,9 @@ typedef struct sim_config {
     uint32_t struct_size;       /* sizeof(sim_config) */
     int32_t mode;               /* SIM_MODE_* */
     int32_t kernel;             /* SIM_KERNEL_* */
-    uint32_t target_processes;  /* SLB target count; 0 = 8 per SM (LANE_OP/AUTO), 4 per SM (LANE_INST) */
+    uint32_t target_processes;  /* SLB target count; 0 = by mapping: one instance 4 per SM (8 when that leaves a
+                                   straggler well above the slowest fiber), cluster exchange one per warp of the
+                                   resident clusters, lane = instance 4 per SM (bytecode) or 2 (generated) */
     uint32_t warps_per_cta;     /* 0 = autotuned */
     uint32_t max_slots;         /* per-process value-slot cap; 0 = from the shared-memory budget */
     uint32_t digest_capacity;   /* per-cycle digest ring length in cycles; 0 = digests off */

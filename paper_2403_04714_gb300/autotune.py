@@ -44,15 +44,15 @@ def _key(text: bytes, n_inst: int, device: str) -> str:
 def default_candidates(n_inst: int, sms: int = 152):
     if n_inst >= 32:
         # each warp's staging area of shared memory bounds the warps per SM:
-        # smaller CTAs let more of them share an SM.  Two processes per SM
-        # instead of four: fewer fibers duplicated across processes (mid: 210k
-        # instead of 220k generated instructions per instance-cycle) and
-        # fewer spills; measured 4-7 % faster on the 200k-op netlist
+        # smaller CTAs let more of them share an SM.  The default partition
+        # has two processes per SM (fewer fibers duplicated across processes
+        # than with four: mid 210k instead of 220k generated instructions per
+        # instance-cycle, measured 4-7 % faster); four stay candidates
         return ([dict(mode="lane_inst", lowering="generated", warps_per_cta=w, task_order="process_major")
                  for w in (12, 8, 6, 4)] +
                 [dict(mode="lane_inst", lowering="generated", warps_per_cta=8, task_order="group_major")] +
                 [dict(mode="lane_inst", lowering="generated", warps_per_cta=w, task_order="process_major",
-                      target_processes=2 * sms) for w in (12, 8)])
+                      target_processes=4 * sms) for w in (12, 8)])
     # operator pairs chained in one step (chain=2) measured faster on every
     # geometry; the unchained adaptive geometry stays as the reference
     cands = [dict(mode="lane_op", lowering="bytecode", chain=0),              # adaptive: 4 or 8 per SM

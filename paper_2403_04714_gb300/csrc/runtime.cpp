@@ -278,14 +278,19 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
         pc.hypergraph = h->cfg.partitioner == SIM_PART_HYPERGRAPH;
         uint32_t target = h->cfg.target_processes;
         // defaults measured on GB300: one process per warp of 8-warp CTAs for a
-        // single instance; four processes per SM with lane = instance; with
-        // cluster exchange one process per warp of every resident cluster CTA
+        // single instance; with lane = instance four processes per SM for the
+        // bytecode and two for generated code (fewer fibers duplicated across
+        // processes: mid x 4,096 15.0-15.2M against 14.2-14.4M
+        // instance-cycles/s at four); with cluster exchange one process per
+        // warp of every resident cluster CTA
         if (!target && h->cfg.cluster_size >= 2 && h->cfg.cluster_size <= 16) {
             const uint32_t W = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
             target = uint32_t(resident_clusters(h->cfg.cluster_size, W)) * h->cfg.cluster_size * W;
         }
         const bool adaptive = !target && h->cfg.mode != SIM_MODE_LANE_INST;
-        if (!target) target = uint32_t(sm_count()) * 4;
+        if (!target)
+            target = uint32_t(sm_count()) *
+                     (h->cfg.mode == SIM_MODE_LANE_INST && h->cfg.lowering == SIM_LOWER_GENERATED ? 2 : 4);
         pc.target = target;
         rc = partition(h->nl, pc, h->part, err);
         if (rc) return set_err(rc, err);

@@ -193,9 +193,12 @@ static __device__ void final_commit(const DevProg& P, const DevState& S, uint64_
 __device__ __forceinline__ void fill_stim(const DevProg& P, const DevState& S, uint64_t t, uint64_t tid,
                                           uint64_t nth) {
     uint64_t* out = S.stim[t & 1];
-    const uint64_t n = (uint64_t)P.n_in * S.I;
+    const uint32_t I = S.I;
+    const uint64_t n = (uint64_t)P.n_in * I;
+    const bool small = n <= 0xffffffffull;     // 32-bit division (the usual case)
     for (uint64_t e = tid; e < n; e += nth) {
-        const uint32_t k = uint32_t(e / S.I), inst = uint32_t(e % S.I);
+        const uint32_t k = small ? uint32_t(e) / I : uint32_t(e / I);
+        const uint32_t inst = small ? uint32_t(e) - k * I : uint32_t(e % I);
         out[e] = stimulus(P, S, S.key[inst], k, inst, t, P.in_w[k]);
     }
 }
