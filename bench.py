@@ -36,7 +36,7 @@ STATE_BYTES_MID = 6126 / 8 + 7955 * 4 + 5927 * 8
 # per-cycle exchange stays in L2 (capture: ncu --metrics dram__bytes_read.sum,
 # dram__bytes_write.sum -k regex:k_cycles -s 1 -c 1 on `bench.py --no-rows
 # --steps 2 --warmup 1`, operator pairs in 2-CTA clusters, hypergraph partition)
-HEADLINE_TRAFFIC = 5.115e6 + 0.099e6
+HEADLINE_TRAFFIC = 5.218e6 + 0.104e6
 HBM_PEAK_GBS = 6790.0       # overwritten from MEASURED_PEAKS.json when present
 WORKLOAD = ("mid netlist: 200k ops, 20k registers (30% 1b / 40% 32b / 30% 64b), depth 60, "
             "fan-out power law (alpha 2, max 512), two 512x64b synchronous RAMs; 1 instance, "
