@@ -53,6 +53,11 @@ constexpr uint32_t kStepLeaf = 1u << 30;
 // from a register (their slot fields name that result's slot, so the two
 // rows also read as sequential steps).
 constexpr uint32_t kStepChain = 1u << 29;
+// A store step (also kStepGeneric) holds only register stores (D_STR) and
+// mirror stores (D_STX), up to kLeafStepMax of them, four per lane.  Only
+// programs without operator pairs have them (measured: with pairs the store
+// step's code slows the pair loop more than the steps it saves).
+constexpr uint32_t kStepStore = 1u << 28;
 constexpr uint32_t kStepRowsShift = 24;
 constexpr uint32_t kStepRowsMask = 0xfu;
 constexpr uint32_t kChainMax = 2;

@@ -1802,19 +1802,22 @@ int lower(const Netlist& nl, const Partition& part, Lowered& out, std::string& e
         } else {
             // compact copy: the occupied lanes of each row; up to four rows of
             // leaves (which never share a slot: all their consumers come later)
-            // form one wide step of up to 128 instructions
+            // form one wide step of up to 128 instructions, and so do up to
+            // four rows of register stores
             std::vector<uint32_t> count(nb, 0);
             for (size_t k = 0; k < items.size(); k++) count[bundle[k]]++;
             std::vector<CStep> steps;
             for (uint32_t b = 0; b < nb; b++) {
                 const DIns* row = &out.s_ins[(size_t(out.s_off[p]) + b) * 32];
-                bool operators_only = true, leaves_only = count[b] > 0;
+                bool operators_only = true, leaves_only = count[b] > 0, stores_only = count[b] > 0;
                 for (uint32_t l = 0; l < count[b]; l++) {
                     operators_only &= row[l].op >= D_ADD && row[l].op <= D_CONCAT;
                     leaves_only &= row[l].op == D_LDR || row[l].op == D_LDI || row[l].op == D_CONST;
+                    stores_only &= row[l].op == D_STR;
                 }
-                const uint32_t flags = (operators_only ? 0u : kStepGeneric) | (leaves_only ? kStepLeaf : 0u);
-                if (leaves_only && !steps.empty() && (steps.back().flags & kStepLeaf) &&
+                const uint32_t wide = leaves_only ? kStepLeaf : stores_only ? kStepStore : 0u;
+                const uint32_t flags = (operators_only ? 0u : kStepGeneric) | wide;
+                if (wide && !steps.empty() && (steps.back().flags & wide) &&
                     steps.back().ins.size() + count[b] <= kLeafStepMax) {
                     steps.back().ins.insert(steps.back().ins.end(), row, row + count[b]);
                     continue;
@@ -1923,7 +1926,7 @@ std::vector<CStep> read_steps(const Lowered& low, size_t p) {
     std::vector<CStep> steps(nb);
     for (uint32_t b = 0; b < nb; b++) {
         const uint32_t e = w[1 + b], first = e & 0xffff, cnt = (e >> 16) & kStepCountMask;
-        steps[b].flags = e & (kStepGeneric | kStepLeaf | kStepChain | (kStepRowsMask << kStepRowsShift));
+        steps[b].flags = e & (kStepGeneric | kStepLeaf | kStepChain | kStepStore | (kStepRowsMask << kStepRowsShift));
         steps[b].ins.assign(ins + first, ins + first + cnt);
     }
     return steps;
@@ -1932,7 +1935,7 @@ std::vector<CStep> read_steps(const Lowered& low, size_t p) {
 }  // namespace
 
 int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_t W, Lowered& low, ClusterPlan& plan,
-                   std::string& err) {
+                   std::string& err, bool wide_stores) {
     const size_t NP = part.procs.size();
     if (C < 1 || W < 1 || NP == 0) { err = "cluster lowering: bad geometry"; return SIM_ERR_BADARG; }
     const uint32_t G = C * W;                                   // processes per cluster
@@ -2151,10 +2154,19 @@ int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_
                     }
                 }
             }
-        for (size_t k = 0; k < stx.size(); k += 32) {
+        // without operator pairs: into the last store step while it has
+        // room, then new store steps; with them: steps of 32
+        const size_t width = wide_stores ? kLeafStepMax : 32;
+        size_t k = 0;
+        if (wide_stores && !steps[p].empty() && (steps[p].back().flags & kStepStore)) {
+            auto& last = steps[p].back().ins;
+            k = std::min(stx.size(), width - std::min(width, last.size()));
+            last.insert(last.end(), stx.begin(), stx.begin() + k);
+        }
+        for (; k < stx.size(); k += width) {
             CStep st;
-            st.flags = kStepGeneric;
-            st.ins.assign(stx.begin() + k, stx.begin() + std::min(stx.size(), k + 32));
+            st.flags = kStepGeneric | (wide_stores ? kStepStore : 0u);
+            st.ins.assign(stx.begin() + k, stx.begin() + std::min(stx.size(), k + width));
             steps[p].push_back(std::move(st));
         }
     }

@@ -132,9 +132,11 @@ struct ClusterPlan {
     uint64_t reads_local = 0;          // cross-process register reads inside a cluster
     uint64_t reads_remote = 0;         // ... and across clusters
 };
-// Rewrites the LANE_OP tables of `low` (bundles and compact programs).
+// Rewrites the LANE_OP tables of `low` (bundles and compact programs); with
+// `wide_stores` (programs without operator pairs) the mirror stores join the
+// wide store steps.
 int lower_clusters(const Netlist& nl, const Partition& part, uint32_t C, uint32_t W, Lowered& low, ClusterPlan& plan,
-                   std::string& err);
+                   std::string& err, bool wide_stores);
 
 // register index -> (class, index in class)
 struct RegLayout {

@@ -259,6 +259,17 @@ __device__ __forceinline__ uint64_t alu_select(uint32_t op, uint64_t a, uint64_t
     return k3 ? r1 : r0;
 }
 
+// Next value of a register into its plane (one instance per warp: pack == 1).
+template <bool DIGEST>
+__device__ __forceinline__ void store_reg(const Dec& d, uint64_t v, const DevState& S, uint32_t inst, uint32_t nxt,
+                                          int32_t col, uint64_t& dacc) {
+    const uint32_t idx = d.b | (d.x << 16);
+    if (d.c == RC_W64) S.w64[nxt][(uint64_t)idx * S.I + inst] = v;
+    else if (d.c == RC_W32) S.w32[nxt][(uint64_t)idx * S.I + inst] = uint32_t(v);
+    else S.bits[nxt][(uint64_t)idx * S.bit_stride + inst] = uint32_t(v);
+    if (DIGEST && col >= 0) dacc += mix64(((uint64_t)d.imm * kGamma + 1ULL) ^ v);
+}
+
 template <bool DIGEST>
 __device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, const DevState& S, uint32_t inst, uint64_t t,
                                              uint64_t key, int32_t col, bool pending, uint64_t* __restrict__ sl,
@@ -286,15 +297,9 @@ __device__ __forceinline__ void exec_lane_op(const Dec& d, const DevProg& P, con
         sl[d.dst] = mem_read(P, S, d.imm, addr, inst, nxt, pending);
         break;
     }
-    case D_STR: {
-        uint64_t v = sl[d.a] & wmask(d.w);
-        uint32_t idx = d.b | (d.x << 16);
-        if (d.c == RC_W64) S.w64[nxt][(uint64_t)idx * S.I + inst] = v;
-        else if (d.c == RC_W32) S.w32[nxt][(uint64_t)idx * S.I + inst] = uint32_t(v);
-        else S.bits[nxt][(uint64_t)idx * S.bit_stride + inst] = uint32_t(v);   // pack == 1
-        if (DIGEST && col >= 0) dacc += mix64(((uint64_t)d.imm * kGamma + 1ULL) ^ v);
+    case D_STR:
+        store_reg<DIGEST>(d, sl[d.a] & wmask(d.w), S, inst, nxt, col, dacc);
         break;
-    }
     case D_WREC: {
         uint64_t en = sl[d.a] != 0;
         uint64_t addr = sl[d.b] & ((1ULL << d.x) - 1);
@@ -435,6 +440,26 @@ __device__ void task_lane_op_res(const DevProg& P, const DevState& S, uint32_t p
             const bool on = lane < cnt;
             const Dec d = decode(ins[on ? first + lane : first]);
             sl[on ? d.dst : dummy] = eval_op(d, sl[d.a], sl[d.b], sl[d.c]);
+        } else if (!PAIRS && (e & kStepStore)) {
+            // programs without pairs: up to four register or mirror stores per
+            // lane, every slot value loaded before the first store
+            uint4 raw[4];
+            uint64_t v[4];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) {
+                const uint32_t i = k * 32 + lane;
+                raw[k] = ins[first + (i < cnt ? i : 0)];
+                const Dec d = decode(raw[k]);
+                v[k] = sl[d.a] & wmask(d.w);
+            }
+            const uint32_t nxt = uint32_t(t & 1) ^ 1u;
+#pragma unroll
+            for (uint32_t k = 0; k < 4; k++) {
+                if (k * 32 + lane >= cnt) break;
+                const Dec d = decode(raw[k]);
+                if (d.op == D_STX) st_peer_u64(mir_nxt + 8u * (d.b | (d.x << 16)), d.c, v[k]);
+                else store_reg<DIGEST>(d, v[k], S, inst, nxt, col, dacc);
+            }
         } else if (e & kStepLeaf) {
             // up to four leaves per lane, every load in flight before the
             // first value is stored; idle lanes write the spare slot

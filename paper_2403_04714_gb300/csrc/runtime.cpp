@@ -316,7 +316,7 @@ int sim_load_netlist(const void* text, size_t len, const sim_config* cfg, sim_ne
                 return set_err(SIM_ERR_BADARG, "cluster exchange runs the persistent kernel");
             const uint32_t W = h->cfg.warps_per_cta ? h->cfg.warps_per_cta : 8;
             if (W > 32) return set_err(SIM_ERR_BADARG, "warps_per_cta above 32");
-            rc = lower_clusters(h->nl, h->part, C, W, h->low, h->cplan, err);
+            rc = lower_clusters(h->nl, h->part, C, W, h->low, h->cplan, err, h->cfg.chain < 2);
             if (rc) return set_err(rc, err);
         }
         h->layout = reg_layout(h->nl);

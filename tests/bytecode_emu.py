@@ -44,8 +44,8 @@ class Emu:
             lens = []
             for p in range(len(c_off)):
                 # word 0: step count; then the step words; instructions from
-                # the next multiple of 4 words.  A wide leaf step (up to 128
-                # independent leaves) becomes several 32-lane rows.
+                # the next multiple of 4 words.  A wide leaf or store step (up
+                # to 128 independent instructions) becomes several 32-lane rows.
                 prog = words[int(c_off[p]):int(c_off[p]) + int(c_size[p])]
                 nb = int(prog[0])
                 table = prog[1:1 + nb]
@@ -56,8 +56,8 @@ class Emu:
                     first, cnt = int(e) & 0xffff, (int(e) >> 16) & 0xff
                     chain = (int(e) >> 29) & 1
                     n_rows_step = (int(e) >> 24) & 0xF if chain else 1
-                    assert cnt <= 32 or (int(e) >> 30) & 1 or (chain and cnt <= 32 * n_rows_step), \
-                        "only leaf and chain steps may exceed 32 lanes"
+                    assert cnt <= 32 or (int(e) >> 30) & 1 or (int(e) >> 28) & 1 or \
+                        (chain and cnt <= 32 * n_rows_step), "only leaf, store and chain steps may exceed 32 lanes"
                     # a chain step holds rows of the lanes' operators, each
                     # lane's next operator in the next row (reading the
                     # previous result's slot): as many sequential rows

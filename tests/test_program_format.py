@@ -1,7 +1,8 @@
 """Static checks of the shared-memory programs the per-operation interpreter
 runs (CPU only): the step words describe the instructions exactly, a step's
 flags match its contents (operator steps hold operators only, leaf steps
-leaves only, up to 128 of them), no step writes a slot twice, every operand
+leaves only and store steps register and mirror stores only, up to 128 of
+them, the latter only in programs without operator pairs), no step writes a slot twice, every operand
 slot was written by an earlier step, and no step reads a slot that it also
 writes."""
 import pytest
@@ -13,7 +14,7 @@ ALU = set(range(5, 18))
 D_MUX, D_SLICE = 15, 16
 D_STR, D_WREC, D_COMMIT, D_LDM, D_STX = 18, 19, 20, 21, 22
 LEAVES = {D_LDR, D_LDI, D_CONST, D_LDM}
-GENERIC, LEAF, CHAIN = 1 << 31, 1 << 30, 1 << 29
+GENERIC, LEAF, CHAIN, STORE = 1 << 31, 1 << 30, 1 << 29, 1 << 28
 
 
 def _reads(d):
@@ -100,8 +101,11 @@ def check_programs(nl):
                 assert all(o in ALU for o in ops), (p, b, "operator step holds another kind")
             if e & LEAF:
                 assert all(o in LEAVES for o in ops) and cnt <= 128, (p, b)
+            elif e & STORE:
+                assert e & GENERIC and all(o in (D_STR, D_STX) for o in ops) and cnt <= 128, (p, b)
+                assert nl.config.chain < 2, (p, b, "store steps only without operator pairs")
             else:
-                assert cnt <= 32 or all(o == D_STX for o in ops), (p, b)
+                assert cnt <= 32, (p, b)
             dsts = [writes(d) for d in step if writes(d) is not None]
             assert len(dsts) == len(set(dsts)), (p, b, "slot written twice in one step")
             step_reads = set()
